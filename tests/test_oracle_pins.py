@@ -1,0 +1,393 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes one part of the oracle with an independent route: the worked example
+printed in Appendix C, closed forms (the Gaussian-likelihood marginal likelihood, where
+the Laplace approximation of Eq. (41) is exact), brute force on tiny inputs (an
+independent optimiser plus finite-difference Hessians), eigenvalue routes for
+determinants, the constraint counts of Section 5.2, and the normalisation of the PC prior.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.optimize as so
+import scipy.sparse as sp
+from scipy.integrate import quad
+from scipy.stats import multivariate_normal
+
+from oracle import inla_oracle as O
+from paper_2311_08050_gb300 import synth
+from paper_2311_08050_gb300.synth import CSR, Block, Factor, ModelSpec
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    out, key, rows = {}, None, []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            tok = line.split()
+            try:
+                vals = [float(t) for t in tok]
+                rows.append(vals)
+                continue
+            except ValueError:
+                pass
+            if key is not None:
+                out[key] = np.array(rows) if len(rows) > 1 else np.array(rows[0])
+            key, rows = tok[0], []
+            if len(tok) > 1:
+                rows.append([float(t) for t in tok[1:]])
+    out[key] = np.array(rows) if len(rows) > 1 else np.array(rows[0])
+    return out
+
+
+# ---------------------------------------------------------------------------------
+# Appendix C worked example
+# ---------------------------------------------------------------------------------
+
+def test_appendix_c_kriging_matches_printed_matrices():
+    g = _read_golden("appendix_c_example.txt")
+    eps = float(g["eps"][0])
+    A, Ql, Qe, C = g["A"], np.diag(g["Ql"]), g["Qe"], g["C"].reshape(1, -1)
+    Q = A.T @ Ql @ A + Qe + eps * np.eye(4)
+    # the uncorrected covariance, and the kriging correction of the oracle
+    assert np.max(np.abs(np.linalg.inv(Q) - g["Sigma_un"])) <= 5e-4
+    S_star = O.kriging_covariance(Q, C)
+    assert np.max(np.abs(S_star - g["Sigma_star"])) <= 5e-4
+    # the oracle's kriging mean satisfies the constraint and equals the projection
+    x_u = np.array([0.3, -1.0, 2.0, 0.5])
+    xk = O.kriging_mean(Q, C, x_u)
+    assert abs(float((C @ xk)[0])) < 1e-12
+    # the Woodbury route of Eq. (woodeqn) with the printed pseudo-inverse
+    Qp = np.linalg.pinv(Qe)
+    assert np.max(np.abs(Qp - g["Qe_pinv"])) <= 5e-4
+    Qlike = A.T @ Ql @ A
+    S_wood = Qp - Qp @ np.linalg.solve(np.eye(4) + Qlike @ Qp, Qlike @ Qp)
+    assert np.max(np.abs(S_wood - g["Sigma_star"])) <= 5e-4
+    # kriging (with eps) and Woodbury/pinv differ by O(eps) only
+    assert np.max(np.abs(S_wood - S_star)) < 10 * eps
+
+
+# ---------------------------------------------------------------------------------
+# small model builders
+# ---------------------------------------------------------------------------------
+
+def _ring_graph(n):
+    cols = [np.array(sorted({(i - 1) % n, (i + 1) % n})) for i in range(n)]
+    return CSR.from_rows(n, n, cols, [np.ones(len(c)) for c in cols])
+
+
+def _dense_gauss_model(seed, n=12, m=30, tau=7.0, with_offset=True):
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(0, 1, (n, 2))
+    cols = [np.array([rng.integers(0, n)]) for _ in range(m)]
+    vals = [np.array([rng.uniform(0.5, 1.5)]) for _ in range(m)]
+    A = CSR.from_rows(m, n, cols, vals)
+    y = rng.standard_normal(m)
+    off = 0.1 * rng.standard_normal(m) if with_offset else None
+    blk = Block("dense_exp", n, points=pts, theta_sigma=0, theta_range_x=1, theta_range_y=2,
+                theta_iid=3, nugget=1e-6)
+    prior = [("gauss", 0.0, 1.0), ("gauss", -1.0, 0.5), ("gauss", -1.0, 0.5), ("pc_prec", 1.0, 0.01)]
+    return ModelSpec("tiny_gauss", n, "gaussian", A, y, off, [blk], prior, lik_prec=tau)
+
+
+def _structured_model(seed, likelihood, m=40):
+    """intercept + ICAR(5) (eps) + iid(5) + RW1(4) (eps) + ICAR x RW1 (eps), with
+    constraints that span the null space of every intrinsic block."""
+    rng = np.random.default_rng(seed)
+    g = _ring_graph(5)
+    blocks = [Block("fixed", 1, prec=1e-3),
+              Block("kron", 5, theta_idx=0, factors=[Factor("icar", 5, g)], eps=1e-5),
+              Block("iid", 5, theta_idx=1),
+              Block("kron", 4, theta_idx=2, factors=[Factor("rw1", 4)], eps=1e-5),
+              Block("kron", 20, theta_idx=3, factors=[Factor("icar", 5, g), Factor("rw1", 4)], eps=1e-5)]
+    n = 35
+    cols, vals = [], []
+    for i in range(m):
+        s, t = rng.integers(0, 5), rng.integers(0, 4)
+        cols.append(np.array([0, 1 + s, 6 + s, 11 + t, 15 + 4 * s + t]))
+        vals.append(np.ones(5))
+    A = CSR.from_rows(m, n, cols, vals)
+    off = rng.normal(0.5, 0.2, m)
+    if likelihood == "poisson":
+        y = rng.poisson(np.exp(off + 0.3 * rng.standard_normal(m))).astype(float)
+    else:
+        y = off + rng.standard_normal(m)
+    crow = [np.arange(1, 6), np.arange(11, 15)]
+    crow += [np.array([15 + 4 * s + t for s in range(5)]) for t in range(4)]
+    crow += [np.array([15 + 4 * s + t for t in range(4)]) for s in range(4)]
+    C = CSR.from_rows(len(crow), n, crow, [np.ones(len(c)) for c in crow])
+    prior = [("pc_prec", 1.0, 0.01)] * 4
+    return ModelSpec("tiny_struct", n, likelihood, A, y, off, blocks, prior, C=C, lik_prec=3.0)
+
+
+def _null_basis(C):
+    """Orthonormal basis of {x : C x = 0} from the SVD of C."""
+    u, s, vt = np.linalg.svd(C)
+    r = int(np.sum(s > 1e-10 * s[0]))
+    return vt[r:].T
+
+
+# ---------------------------------------------------------------------------------
+# closed forms: Gaussian likelihood (Laplace is exact)
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gaussian_marginal_likelihood_closed_form(seed):
+    spec = _dense_gauss_model(seed)
+    theta = np.array([0.2, np.log(0.3), np.log(0.15), np.log(5.0)])
+    r = O.evaluate(spec, theta)
+    # Sigma_x directly (no inversion): covariance of the latent field
+    S = O.exp_covariance(spec.blocks[0], theta)
+    A = spec.A.to_dense()
+    cov_y = A @ S @ A.T + np.eye(spec.m) / spec.lik_prec
+    ref = O.log_theta_prior(spec, theta) + multivariate_normal(spec.offset, cov_y).logpdf(spec.y)
+    assert abs(r["log_post"] - ref) <= 1e-9 * max(1.0, abs(ref))
+    # posterior mean and covariance by the covariance-form (Woodbury) route
+    K = S @ A.T @ np.linalg.inv(cov_y)
+    mean = K @ (spec.y - spec.offset)
+    cov = S - K @ A @ S
+    assert np.max(np.abs(r["x_hat"] - mean)) <= 1e-9 * np.max(np.abs(mean))
+    assert np.max(np.abs(r["var"] - np.diag(cov)) / np.diag(cov)) <= 1e-8
+
+
+def test_gaussian_constrained_closed_form():
+    """Constrained Gaussian model: x = N z with N an orthonormal basis of null(C);
+    z ~ N(0, (N^T Q_p N)^-1) is the prior conditioned on C x = 0, so
+    y ~ N(o, A N (N^T Q_p N)^-1 N^T A^T + tau^-1 I) exactly."""
+    spec = _structured_model(3, "gaussian")
+    theta = np.array([0.5, 1.0, -0.3, 0.8])
+    r = O.evaluate(spec, theta)
+    Qp, _ = O.prior_precision(spec, theta)
+    C = spec.C.to_dense()
+    N = _null_basis(C)
+    Sz = np.linalg.inv(N.T @ Qp @ N)
+    A = spec.A.to_dense()
+    AN = A @ N
+    cov_y = AN @ Sz @ AN.T + np.eye(spec.m) / spec.lik_prec
+    ref = O.log_theta_prior(spec, theta) + multivariate_normal(spec.offset, cov_y).logpdf(spec.y)
+    assert abs(r["log_post"] - ref) <= 1e-8 * max(1.0, abs(ref))
+    # posterior of z, mapped back: mode and marginal variances
+    Pz = N.T @ Qp @ N + spec.lik_prec * AN.T @ AN
+    z = np.linalg.solve(Pz, spec.lik_prec * AN.T @ (spec.y - spec.offset))
+    assert np.max(np.abs(r["x_hat"] - N @ z)) <= 1e-8
+    assert np.max(np.abs(C @ r["x_hat"])) <= 1e-10
+    var = np.diag(N @ np.linalg.inv(Pz) @ N.T)
+    assert np.max(np.abs(r["var"] - var) / var) <= 1e-6
+
+
+# ---------------------------------------------------------------------------------
+# brute force: Poisson Laplace approximation on tiny inputs
+# ---------------------------------------------------------------------------------
+
+def _fd_hessian(f, x, h=1e-4):
+    d = x.size
+    H = np.zeros((d, d))
+    for i in range(d):
+        for j in range(i, d):
+            ei = np.zeros(d); ei[i] = h
+            ej = np.zeros(d); ej[j] = h
+            H[i, j] = H[j, i] = (f(x + ei + ej) - f(x + ei - ej) - f(x - ei + ej) + f(x - ei - ej)) / (4 * h * h)
+    return H
+
+
+def _laplace_bruteforce(spec, theta, N=None):
+    """Mode by scipy BFGS and the Hessian by finite differences, both in the
+    coordinates x = N z (N = I without constraints)."""
+    Qp, logdet_Qp = O.prior_precision(spec, theta)
+    A = spec.A.to_dense()
+    off = np.zeros(spec.m) if spec.offset is None else spec.offset
+    N = np.eye(spec.n) if N is None else N
+
+    def f(z):
+        x = N @ z
+        eta = A @ x + off
+        return float(np.sum(spec.y * eta - np.exp(eta)) - 0.5 * x @ Qp @ x)
+
+    def g(z):
+        x = N @ z
+        eta = A @ x + off
+        return N.T @ (A.T @ (spec.y - np.exp(eta)) - Qp @ x)
+
+    res = so.minimize(lambda z: -f(z), np.zeros(N.shape[1]), jac=lambda z: -g(z), method="BFGS",
+                      options=dict(gtol=1e-11, maxiter=10000))
+    z = res.x
+    H = -_fd_hessian(f, z)
+    x = N @ z
+    const = -float(np.sum(__import__("scipy.special", fromlist=["gammaln"]).gammaln(spec.y + 1)))
+    lp = (O.log_theta_prior(spec, theta) + f(z) + const
+          + 0.5 * np.linalg.slogdet(N.T @ Qp @ N)[1] - 0.5 * np.linalg.slogdet(H)[1])
+    return lp, x
+
+
+def test_poisson_laplace_bruteforce_unconstrained():
+    rng = np.random.default_rng(7)
+    n, m = 4, 9
+    cols = [np.array([0, 1 + rng.integers(0, 3)]) for _ in range(m)]
+    A = CSR.from_rows(m, n, cols, [np.array([1.0, rng.uniform(0.5, 1.5)]) for _ in range(m)])
+    y = rng.poisson(2.0, m).astype(float)
+    blocks = [Block("fixed", 1, prec=1e-3), Block("iid", 3, theta_idx=0)]
+    spec = ModelSpec("tiny_pois", n, "poisson", A, y, None, blocks, [("pc_prec", 1.0, 0.01)])
+    theta = np.array([0.7])
+    r = O.evaluate(spec, theta)
+    ref, x = _laplace_bruteforce(spec, theta)
+    assert np.max(np.abs(r["x_hat"] - x)) < 1e-6
+    assert abs(r["log_post"] - ref) < 1e-5
+    # Newton converged to a stationary point of the log posterior
+    As = sp.csr_matrix(spec.A.to_dense())
+    Qp, _ = O.prior_precision(spec, theta)
+    grad = As.T @ (y - np.exp(As @ r["x_hat"])) - Qp @ r["x_hat"]
+    assert np.max(np.abs(grad)) < 1e-9
+
+
+def test_poisson_laplace_bruteforce_constrained():
+    spec = _structured_model(11, "poisson", m=30)
+    theta = np.array([0.3, 1.2, -0.2, 0.5])
+    r = O.evaluate(spec, theta)
+    N = _null_basis(spec.C.to_dense())
+    ref, x = _laplace_bruteforce(spec, theta, N)
+    assert np.max(np.abs(r["x_hat"] - x)) < 1e-6
+    assert abs(r["log_post"] - ref) < 1e-5
+    assert np.max(np.abs(spec.C.to_dense() @ r["x_hat"])) < 1e-10
+
+
+# ---------------------------------------------------------------------------------
+# determinants / inverses by an independent route
+# ---------------------------------------------------------------------------------
+
+def test_prior_logdet_by_eigenvalues():
+    spec = _structured_model(5, "poisson")
+    theta = np.array([0.1, -0.4, 0.9, 1.3])
+    Qp, logdet = O.prior_precision(spec, theta)
+    # Kronecker blocks: eigenvalues of R1 kron R2 are the products of the factors'
+    ld = 0.0
+    for blk in spec.blocks:
+        if blk.kind == "fixed":
+            ld += blk.size * math.log(blk.prec)
+        elif blk.kind == "iid":
+            ld += blk.size * theta[blk.theta_idx]
+        else:
+            ev = np.ones(1)
+            for f in blk.factors:
+                ev = np.kron(ev, np.linalg.eigvalsh(O.structure_matrix(f)))
+            ld += np.sum(np.log(math.exp(theta[blk.theta_idx]) * np.clip(ev, 0, None) + blk.eps))
+    assert abs(logdet - ld) < 1e-8 * abs(ld)
+    assert abs(logdet - np.sum(np.log(np.linalg.eigvalsh(Qp)))) < 1e-8 * abs(ld)
+
+
+def test_dense_block_precision_is_inverse_covariance():
+    spec = _dense_gauss_model(4, n=20)
+    theta = np.array([-0.3, np.log(0.4), np.log(0.2), np.log(2.0)])
+    Qp, logdet = O.prior_precision(spec, theta)
+    S = O.exp_covariance(spec.blocks[0], theta)
+    assert np.max(np.abs(Qp @ S - np.eye(20))) < 1e-9
+    assert abs(logdet + np.sum(np.log(np.linalg.eigvalsh(S)))) < 1e-9 * abs(logdet)
+    # covariance: distance-1 points correlate by exp(-1) (closed-form special case)
+    blk = Block("dense_exp", 2, points=np.array([[0.0, 0.0], [0.3, 0.0]]), theta_sigma=0,
+                theta_range_x=1, theta_range_y=2, nugget=0.0)
+    S2 = O.exp_covariance(blk, np.array([0.0, np.log(0.3), np.log(5.0)]))
+    assert abs(S2[0, 1] - math.exp(-1.0)) < 1e-15
+
+
+# ---------------------------------------------------------------------------------
+# hyperparameter prior
+# ---------------------------------------------------------------------------------
+
+def test_pc_prior_normalised_and_tail_probability():
+    spec = ModelSpec("p", 1, "poisson", CSR(0, 1, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                     np.zeros(0)), np.zeros(0), None, [], [("pc_prec", 1.0, 0.01)])
+    dens = lambda t: math.exp(O.log_theta_prior(spec, [t]))
+    total = quad(dens, -40, 60, limit=400)[0]
+    assert abs(total - 1.0) < 1e-8
+    # P(sigma > U) = P(theta < -2 log U) = alpha, with U = 1
+    assert abs(quad(dens, -60, 0.0, limit=400)[0] - 0.01) < 1e-8
+    g = ModelSpec("g", 1, "poisson", spec.A, np.zeros(0), None, [], [("gauss", 0.5, 2.0)])
+    assert abs(O.log_theta_prior(g, [1.5]) - math.log(0.5 / math.sqrt(2 * math.pi)
+                                                      * math.exp(-0.125))) < 1e-14
+
+
+# ---------------------------------------------------------------------------------
+# constraint counts of Section 5.2 and the workload's constraint matrix
+# ---------------------------------------------------------------------------------
+
+def _rank(R, tol=1e-9):
+    ev = np.linalg.eigvalsh(R)
+    return int(np.sum(ev > tol * ev[-1]))
+
+
+def test_constraint_counts_match_null_space_dimensions():
+    rng = np.random.default_rng(0)
+    Rs = O.structure_matrix(Factor("icar", 50, synth.delaunay_graph(rng, 50)))
+    rs = _rank(Rs)
+    assert rs == 49  # connected planar graph
+    # Spain model: RW1 time (25) x RW1 age (9) x Besag space (50), mains + pairwise + 3-way
+    rt, ra = _rank(O.structure_matrix(Factor("rw1", 25))), _rank(O.structure_matrix(Factor("rw1", 9)))
+    nt, na, ns = 25, 9, 50
+    null = lambda sizes, ranks: int(np.prod(sizes) - np.prod(ranks))
+    k = (3 + null([nt, na], [rt, ra]) + null([nt, ns], [rt, rs]) + null([ns, na], [rs, ra])
+         + null([ns, nt, na], [rs, rt, ra]))
+    # paper's per-term formulas n_t n_a - (n_t-1)(n_a-1) etc. and its total
+    assert null([nt, na], [rt, ra]) == nt * na - (nt - 1) * (na - 1)
+    assert k == 2010
+    # Table 3: RW2 time (5) + Besag space (200) + time x space: k = n_t + 2 n_s + 1
+    for ns_ in (200, 400, 800):
+        g = synth.delaunay_graph(np.random.default_rng(ns_), ns_)
+        rs_ = _rank(O.structure_matrix(Factor("icar", ns_, g)))
+        rt2 = _rank(O.structure_matrix(Factor("rw2", 5)))
+        k3 = (5 - rt2) + (ns_ - rs_) + null([5, ns_], [rt2, rs_])
+        assert k3 == 5 + 2 * ns_ + 1
+    assert [5 + 2 * s + 1 for s in (200, 400, 800)] == [406, 806, 1606]
+
+
+def test_workload_constraints_span_the_intrinsic_null_spaces():
+    spec, _ = synth.config3()
+    C = sp.csr_matrix((spec.C.val, spec.C.col, spec.C.rowptr), shape=(spec.k, spec.n))
+    assert spec.k == 1486 and spec.n == 8149
+    # C Q_p = eps C for the intrinsic blocks, i.e. C R = 0 blockwise
+    start = 0
+    R_blocks = []
+    for blk in spec.blocks:
+        if blk.kind == "kron":
+            R = sp.csr_matrix(np.ones((1, 1)))
+            for f in blk.factors:
+                R = sp.kron(R, sp.csr_matrix(O.structure_matrix(f)))
+            R_blocks.append(R)
+        else:
+            R_blocks.append(sp.csr_matrix((blk.size, blk.size)))
+        start += blk.size
+    R = sp.block_diag(R_blocks).tocsr()
+    assert abs(C @ R).max() < 1e-12
+    # full row rank: C C^T is positive definite
+    CCt = (C @ C.T).toarray()
+    assert np.all(np.diag(np.linalg.cholesky(CCt)) > 1e-8)
+
+
+# ---------------------------------------------------------------------------------
+# invariance
+# ---------------------------------------------------------------------------------
+
+def test_log_post_invariant_to_latent_permutation():
+    spec, thetas = synth.config1()
+    r = O.evaluate(spec, thetas[1], want_var=True)
+    perm = np.random.default_rng(3).permutation(255)
+    blk = spec.blocks[1]
+    pts = blk.points[perm]
+    inv = np.argsort(perm)
+    col = spec.A.col.copy()
+    mask = col >= 1
+    col[mask] = 1 + inv[col[mask] - 1]
+    A2 = CSR(spec.A.nrows, spec.A.ncols, spec.A.rowptr, col, spec.A.val)
+    b2 = Block("dense_exp", 255, points=pts, theta_sigma=0, theta_range_x=1, theta_range_y=1,
+               nugget=blk.nugget)
+    spec2 = ModelSpec("perm", spec.n, "poisson", A2, spec.y, None, [spec.blocks[0], b2],
+                      spec.theta_prior)
+    r2 = O.evaluate(spec2, thetas[1])
+    assert abs(r["log_post"] - r2["log_post"]) < 1e-9 * abs(r["log_post"])
+    assert np.max(np.abs(r["x_hat"][1:][perm] - r2["x_hat"][1:])) < 1e-9
+    assert np.max(np.abs(r["var"][1:][perm] / r2["var"][1:] - 1)) < 1e-9
