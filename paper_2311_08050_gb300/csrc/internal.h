@@ -1,0 +1,135 @@
+// Internal declarations of libinla (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+#include <string>
+#include "../../include/inla.h"
+
+namespace inla {
+
+constexpr int TB = 64;        // FP64 tile edge
+constexpr int PAD = 256;      // latent and dense-block padding unit
+constexpr int MAX_THETA = 16;
+constexpr int MAX_KRON = 8;
+
+#define INLA_CUDA_TRY(expr)                                  \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) {                                 \
+      return _e == cudaErrorMemoryAllocation ? INLA_E_NOMEM  \
+                                             : INLA_E_CUDA;  \
+    }                                                        \
+  } while (0)
+
+#define INLA_TRY(expr)            \
+  do {                            \
+    int _s = (expr);              \
+    if (_s != INLA_OK) return _s; \
+  } while (0)
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Structured prior entry of Q_p (lower triangle, internal indices):
+// value = a + b * exp(theta[t])  (t < 0: value = a)
+struct PriorEntry {
+  int32_t row, col, t, pad_;
+  double a, b;
+};
+
+// Kronecker block: eigenvalues of its structure for log-determinants.
+struct KronLogdet {
+  int32_t offset;      // into the eigenvalue array
+  int32_t size;
+  int32_t theta_idx;
+  int32_t constrained; // 1: the block's constraints span its null space
+  double eps;
+};
+
+// Device-resident, theta-independent model data.
+struct ModelDev {
+  int32_t n, n_pad, m, k, k_pad, nd, nd_pad;   // nd: dense block size (0 if none)
+  int32_t likelihood;
+  double lik_prec;
+  int32_t theta_dim;
+  // likelihood
+  int64_t *A_rowptr; int32_t *A_col; double *A_val;        // m x n_pad, internal columns
+  int64_t *At_rowptr; int32_t *At_row; double *At_val;     // n_pad x m (transpose)
+  int64_t npairs;
+  int32_t *pair_row, *pair_col; int64_t *pair_ptr;         // unique (row >= col) pairs
+  int32_t *pc_obs; double *pc_coef;                        // contributions
+  double *y, *offset;                                      // offset may be null
+  double lgamma_sum;                                       // sum log y! (Poisson)
+  // prior
+  double *points;                                          // nd x 2
+  int32_t theta_sigma, theta_rx, theta_ry, theta_iid;
+  double nugget;
+  int64_t nentries;
+  PriorEntry *entries;
+  double prior_const_logdet;                               // fixed blocks
+  int32_t nkron;
+  KronLogdet kron[MAX_KRON];
+  double *kron_eig;
+  double logdet_CCt;                                       // constrained blocks
+  int32_t n_iid; int32_t iid_theta[MAX_KRON]; int32_t iid_size[MAX_KRON];
+  // constraints (k x n_pad), internal columns
+  int64_t *C_rowptr; int32_t *C_col; double *C_val;
+  // theta prior
+  int32_t prior_kind[MAX_THETA];
+  double prior_a[MAX_THETA], prior_b[MAX_THETA];
+};
+
+}  // namespace inla
+
+struct inla_model {
+  inla::ModelDev d;
+  std::vector<int32_t> perm;   // perm[original index] = internal index
+  std::vector<void*> allocations;
+  int device;
+};
+
+namespace inla {
+
+// Per-theta working set ("slot"), resident in device memory.
+struct Slot {
+  // matrices, row-major with leading dimension n_pad (k_pad for S)
+  double *Qp;     // prior precision (full symmetric)
+  double *L;      // Q, factored in place (lower)
+  double *Wk;     // dense-block covariance / inverse factor workspace
+  double *Linv;   // n_pad x TB: inverses of the diagonal tiles of L
+  double *Z;      // n_pad x k_pad: L^-1 C^T
+  double *S;      // k_pad x k_pad: Z^T Z, factored
+  double *SLinv;  // k_pad x TB
+  double *Wd;     // nd_pad x TB: inverses of the diagonal tiles of the covariance factor
+  // vectors
+  double *x, *xn, *g, *t1, *t2;    // n_pad
+  double *eta, *w;                 // m
+  double *kv1, *kv2;               // k_pad
+  double *red;                     // reduction scratch (256 doubles)
+  double *out;                     // scalar outputs (SLOT_NOUT doubles)
+  int32_t *info;                   // [0] status flags, [1] failing pivot
+  const ModelDev *md;              // device copy of the model struct
+  int32_t n_pad, n, m, k, k_pad, nd, nd_pad;
+  int32_t active;                  // participates in the current Newton step
+  double theta[MAX_THETA];
+};
+
+// indices into Slot::out
+enum {
+  OUT_LOGDET_COV = 0,   // log|Sigma| of the dense block
+  OUT_LOGDET_Q,         // log|Q*|
+  OUT_LOGDET_S,         // log|C Q*^-1 C^T|
+  OUT_LOGLIK,           // sum log p(y|eta) (without the constant)
+  OUT_QUAD,             // x^T Q_p x
+  OUT_STEP,             // max |x_new - x|
+  OUT_PRIOR_STRUCT,     // structured prior log-det part (incl. constraint terms)
+  OUT_LOG_THETA_PRIOR,  // log pi(theta)
+  OUT_LOGDET_TMP,
+  OUT_LOGPOST,          // log pi~(theta|y)
+  SLOT_NOUT = 16
+};
+
+// info flags
+enum { INFO_NOT_SPD = 1, INFO_TIMEOUT = 2, INFO_NONFINITE = 4 };
+
+}  // namespace inla

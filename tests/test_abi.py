@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads, and exports every entry point include/inla.h declares
+(CPU only: no compute call needs a GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2311_08050_gb300 import build as B
+from paper_2311_08050_gb300 import inla
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "inla.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(inla_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_header_declares_the_binding_entry_points():
+    assert set(inla.EXPORTED) <= set(_declared())
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(inla_[a-z0-9_]+)", out))
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_answers_without_a_gpu(libpath):
+    L = inla.lib()
+    assert inla.status_string(0) == "ok"
+    assert inla.status_string(inla.E_NOT_SPD) == "matrix not positive definite"
+    o = inla.Opts()
+    assert L.inla_opts_default(ctypes.byref(o)) == 0
+    assert o.newton_tol == 1e-8 and o.newton_max == 50 and o.precision == 0
+    # NULL arguments are rejected before any device work
+    assert L.inla_model_create(None, None) == inla.E_BADARG
+    assert L.inla_model_destroy(None) == 0
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets a C compiler gives the header."""
+    structs = {"inla_factor": inla.Factor, "inla_block": inla.BlockS, "inla_model_desc": inla.ModelDesc,
+               "inla_opts": inla.Opts}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "inla.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} __sizeof__ %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "__sizeof__")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
