@@ -1,0 +1,46 @@
+/*
+ * inla_testing.h -- test hooks of libinla (not part of the evaluation API).
+ *
+ * These entry points expose single building blocks of the mixed-precision path so that
+ * tests can check them in isolation against plain FP64 arithmetic.  They allocate their own
+ * device buffers, copy host arrays in and out, and return INLA_OK or a negative INLA_E_*.
+ */
+#ifndef INLA_TESTING_H
+#define INLA_TESTING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = alpha C + beta op(A) op(B)^T with the Ozaki-split tensor-core GEMM (S BF16 slices per
+ * operand, exact FP32 accumulation per 256-wide K chunk, double-float C).
+ * A: row-major M x K (trans_a = 0) or K x M (trans_a = 1); B: N x K or K x N; C: M x N,
+ * all host FP64 arrays.  K must be a multiple of 64.  lower = 1 computes only the lower
+ * triangle (M == N); k_mode restricts K per 128 x 128 tile (0: all; 1: k >= max(row0, col0);
+ * 2: k >= col0; 3: k >= row0).  alpha must be 0 or 1, beta +1 or -1. */
+int inla_test_ozaki_gemm(const double *A, const double *B, double *C, int32_t M, int32_t N, int32_t K,
+                         int32_t slices, int32_t trans_a, int32_t trans_b, int32_t lower, int32_t k_mode,
+                         double alpha, double beta);
+
+/* With the environment variable INLA_DEBUG_SYNC=1 the library synchronizes after each
+ * checked step; this returns the first step at which a CUDA error became visible ("" if
+ * none).  Static storage, owned by the library. */
+const char *inla_test_debug_site(void);
+
+/* Launch statistics of the Ozaki-split tensor-core GEMM (the dominant kernel of the mixed
+ * path).  While enabled, CUDA events are recorded around every launch on its stream.
+ * inla_test_stats_read fills out[0..3] = {launches, algorithmic flops (2 * needed output
+ * elements * K), tensor-pipe flops (algorithmic * S(S+1)/2 BF16 passes), summed launch
+ * time in ms}, synchronizing on the recorded events, and resets the counters. */
+void inla_test_stats_enable(int on);
+int inla_test_stats_read(double *out);
+
+/* Number of CUDA kernels the library launched since the previous call (then reset). */
+int64_t inla_test_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INLA_TESTING_H */

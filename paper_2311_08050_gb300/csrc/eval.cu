@@ -2,22 +2,48 @@
 // (Algorithm 1 of Appendix A.2.1, with conditioning by kriging for C x = 0, Section 5.2),
 // the final factorisation at the mode, log pi~(theta|y) (Eq. (41)) and the Gaussian
 // marginal variances (Appendix A.2.1).  Every point of a batch occupies one "slot"; all
-// kernels of a step run over all active slots at once (grid.y / grid.z = slot).
+// kernels of a step run over all active slots at once (grid.y / grid.z = slot).  Points
+// are grouped by model shape so that a group's matrices have uniform per-slot strides.
 //
 // The Newton step is written as x_new = x + Q*(x)^-1 grad f(x), with
 // grad f(x) = A^T (y - w) - Q_p x: this equals the solve Q* x_new = grad g + Q_l x of
 // Algorithm 1 in exact arithmetic, and its fixed point is the exact mode even when the
-// factor is computed in reduced precision.
-#include "kernels.h"
+// factor is computed in reduced precision (mixed path).
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include "mixed.h"
 
 namespace inla {
 
 void launch_gather(double* dst, const double* src, const int32_t* perm, int n, cudaStream_t st);
+
+int64_t g_kernel_launches = 0;
+static char g_debug_site[256] = "";
+bool debug_sync_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("INLA_DEBUG_SYNC");
+    on = (e && e[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+int debug_check(cudaStream_t st, const char* site) {
+  if (!debug_sync_enabled()) return INLA_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (!g_debug_site[0]) snprintf(g_debug_site, sizeof(g_debug_site), "%s: %s", site, cudaGetErrorString(e));
+    return INLA_E_CUDA;
+  }
+  return INLA_OK;
+}
 
 // -------------------------------------------------------------------------------------
 // device workspace arena (grow-only, process wide)
@@ -48,6 +74,7 @@ static int arena_reserve(size_t bytes, int device) {
   return INLA_OK;
 }
 
+// bump allocator over a base pointer; with base == nullptr it only measures
 struct Carve {
   char* p;
   size_t off = 0;
@@ -55,52 +82,16 @@ struct Carve {
   template <typename T>
   T* take(size_t count) {
     off = (off + 255) & ~(size_t)255;
-    T* r = reinterpret_cast<T*>(p + off);
+    T* r = p ? reinterpret_cast<T*>(p + off) : nullptr;
     off += count * sizeof(T);
     return r;
   }
 };
 
-static size_t slot_bytes(const ModelDev& d, bool want_var) {
-  (void)want_var;
-  const size_t np = d.n_pad, kp = d.k_pad;
-  size_t b = 0;
-  auto add = [&](size_t bytes) { b += (bytes + 255) & ~(size_t)255; };
-  add(np * np * 8);            // Qp
-  add(np * np * 8);            // L
-  add(np * np * 8);            // Wk
-  add(np * TB * 8);            // Linv
-  add(std::max<size_t>(d.nd_pad, 1) * TB * 8);  // Wd
-  if (kp) {
-    add(np * kp * 8);  // Z
-    add(kp * kp * 8);  // S
-    add(kp * TB * 8);  // SLinv
-    add(kp * 8);
-    add(kp * 8);
-  }
-  for (int v = 0; v < 5; ++v) add(np * 8);
-  add(std::max<size_t>(d.m, 1) * 8);
-  add(std::max<size_t>(d.m, 1) * 8);
-  add(256 * 8);
-  add(SLOT_NOUT * 8);
-  add(2 * 4);
-  add(sizeof(ModelDev));
-  return b + 4096;
-}
-
 // -------------------------------------------------------------------------------------
-// batched blocked routines (host loops over tile steps)
+// FP64 blocked routines (host loops over tile steps)
 // -------------------------------------------------------------------------------------
-struct Batch {
-  Slot* d_slots;          // device array
-  std::vector<Slot> h;    // host mirror
-  int n;                  // number of slots
-  int max_t, max_td, max_tk, max_m, max_n, max_k;
-  int64_t max_entries, max_pairs;
-  cudaStream_t st;
-};
-
-static void potrf(Batch& B, int sel) {
+static void potrf64(Batch& B, int sel) {
   const int T = sel == SEL_L ? B.max_t : sel == SEL_COV ? B.max_td : B.max_tk;
   for (int kt = 0; kt < T; ++kt) {
     launch_potrf_diag(B.d_slots, B.n, sel, kt, T, B.st);
@@ -108,50 +99,124 @@ static void potrf(Batch& B, int sel) {
     launch_syrk_update(B.d_slots, B.n, sel, kt, T, B.st);
   }
 }
-
-static void trtri(Batch& B, int sel, int dst) {
+static void trtri64(Batch& B, int sel, int dst) {
   const int T = sel == SEL_L ? B.max_t : B.max_td;
-  for (int jt = T - 1; jt >= 0; --jt)
-    launch_trtri_step(B.d_slots, B.n, sel, dst, jt, T, B.st);
-}
-
-// dst = M^-1 src for the factor M = L L^T selected by sel (vectors by id)
-static void solve_llt(Batch& B, int sel, int src, int tmp, int dst) {
-  const int T = sel == SEL_L ? B.max_t : B.max_tk;
-  for (int kt = 0; kt < T; ++kt) launch_trsv_fwd_step(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
-  for (int kt = T - 1; kt >= 0; --kt) launch_trsv_bwd_step(B.d_slots, B.n, sel, tmp, dst, kt, T, B.st);
-}
-static void solve_lt(Batch& B, int sel, int src, int dst) {
-  const int T = sel == SEL_L ? B.max_t : B.max_tk;
-  for (int kt = T - 1; kt >= 0; --kt) launch_trsv_bwd_step(B.d_slots, B.n, sel, src, dst, kt, T, B.st);
+  for (int jt = T - 1; jt >= 0; --jt) launch_trtri_step(B.d_slots, B.n, sel, dst, jt, T, B.st);
 }
 
 enum { V_G = 0, V_T1 = 1, V_T2 = 2, V_KV1 = 3, V_KV2 = 4 };
 
+// dst = M^-1 src for M = L L^T selected by sel; tmp receives L^-1 src
+static void solve_llt(Batch& B, int sel, int src, int tmp, int dst) {
+  const int T = sel == SEL_L ? B.max_t : B.max_tk;
+  for (int kt = 0; kt < T; ++kt) {
+    if (B.mixed) launch_trsv_fwd_df(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
+    else launch_trsv_fwd_step(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
+  }
+  for (int kt = T - 1; kt >= 0; --kt) {
+    if (B.mixed) launch_trsv_bwd_df(B.d_slots, B.n, sel, tmp, dst, kt, B.st);
+    else launch_trsv_bwd_step(B.d_slots, B.n, sel, tmp, dst, kt, T, B.st);
+  }
+}
+static void solve_lt(Batch& B, int sel, int src, int dst) {
+  const int T = sel == SEL_L ? B.max_t : B.max_tk;
+  for (int kt = T - 1; kt >= 0; --kt) {
+    if (B.mixed) launch_trsv_bwd_df(B.d_slots, B.n, sel, src, dst, kt, B.st);
+    else launch_trsv_bwd_step(B.d_slots, B.n, sel, src, dst, kt, T, B.st);
+  }
+}
+
+// ---- precision-dispatched steps ----
+static int op_potrf(Batch& B, int sel) {
+  if (B.mixed) return mixed_potrf(B, sel);
+  potrf64(B, sel);
+  return INLA_OK;
+}
+static void op_logdet(Batch& B, int sel, int out) {
+  if (B.mixed) launch_logdet_df(B.d_slots, B.n, sel, out, B.st);
+  else launch_logdet(B.d_slots, B.n, sel, out, B.st);
+}
+static void op_qp_gemv(Batch& B, int which) {
+  if (B.mixed) {
+    launch_qp_gemv_df(B.d_slots, B.n, which, B.max_n, B.st);
+    launch_quad(B.d_slots, B.n, which, B.st);
+  } else {
+    launch_qp_gemv(B.d_slots, B.n, which, B.max_n, B.st);
+  }
+}
+static void op_assemble_q(Batch& B) {
+  launch_copy_qp_to_l(B.d_slots, B.n, B.max_t, B.st);  // bit copy (FP64 or df64 elements)
+  if (B.mixed) launch_add_pairs_df(B.d_slots, B.n, B.max_pairs, B.st);
+  else launch_add_pairs(B.d_slots, B.n, B.max_pairs, B.st);
+  if (B.max_k > 0) {  // Q* + gamma C^T C: same kriged results, conditioned null directions
+    if (B.mixed) launch_add_cct_df(B.d_slots, B.n, B.st);
+    else launch_add_cct(B.d_slots, B.n, B.st);
+  }
+}
 // Z = L^-1 C^T, S = Z^T Z, factor S
-static void constraint_schur(Batch& B) {
+static int op_schur(Batch& B) {
+  if (B.mixed) return mixed_schur(B);
   for (int i = 0; i < B.n; ++i)
-    if (B.h[i].active && B.h[i].k > 0)
-      cudaMemsetAsync(B.h[i].Z, 0, (size_t)B.h[i].n_pad * B.h[i].k_pad * 8, B.st);
+    if (B.h[i].active && B.h[i].k > 0) cudaMemsetAsync(B.h[i].Z, 0, (size_t)B.h[i].n_pad * B.h[i].k_pad * 8, B.st);
   launch_ct_fill(B.d_slots, B.n, B.max_k, B.st);
   for (int kt = 0; kt < B.max_t; ++kt) launch_fwd_rhs_step(B.d_slots, B.n, kt, B.max_t, B.max_tk, B.st);
   launch_schur_syrk(B.d_slots, B.n, B.max_tk, B.max_t, B.st);
-  potrf(B, SEL_S);
+  potrf64(B, SEL_S);
+  return INLA_OK;
+}
+static int op_prior_dense(Batch& B) {
+  launch_cov_build(B.d_slots, B.n, B.max_td, B.st);
+  if (B.mixed) {
+    launch_cov_to_df(B.d_slots, B.n, B.max_td, B.st);
+    INLA_TRY(mixed_potrf(B, SEL_COV));
+    launch_logdet_df(B.d_slots, B.n, SEL_COV, OUT_LOGDET_COV, B.st);
+    INLA_TRY(mixed_inverse_factor(B, SEL_COV, false));
+    return mixed_lauum_cov(B);
+  }
+  potrf64(B, SEL_COV);
+  launch_logdet(B.d_slots, B.n, SEL_COV, OUT_LOGDET_COV, B.st);
+  trtri64(B, SEL_COV, DST_L);
+  launch_lauum_cov(B.d_slots, B.n, B.max_td, B.st);
+  return INLA_OK;
+}
+static int op_variances(Batch& B) {
+  if (B.mixed) {
+    INLA_TRY(mixed_inverse_factor(B, SEL_L, true));
+    launch_colsumsq_wk_df(B.d_slots, B.n, B.max_t, B.st);
+    if (B.max_k > 0) {
+      INLA_TRY(mixed_var_constraint(B));
+      launch_var_finish(B.d_slots, B.n, B.max_n, B.st);
+    }
+    return INLA_OK;
+  }
+  trtri64(B, SEL_L, DST_WK);
+  launch_colsumsq_wk(B.d_slots, B.n, B.max_t, B.st);
+  if (B.max_k > 0) {
+    launch_zt_w(B.d_slots, B.n, B.max_tk, B.max_t, B.st);
+    for (int kt = 0; kt < B.max_tk; ++kt) launch_fwd_s_rhs_step(B.d_slots, B.n, kt, B.max_tk, B.max_t, B.st);
+    launch_colsumsq_gt(B.d_slots, B.n, B.max_tk, B.max_t, B.st);
+    launch_var_finish(B.d_slots, B.n, B.max_n, B.st);
+  }
+  return INLA_OK;
 }
 
 static void sync_active(Batch& B) {
   cudaMemcpyAsync(B.d_slots, B.h.data(), sizeof(Slot) * B.n, cudaMemcpyHostToDevice, B.st);
 }
 
-static int read_outputs(Batch& B, std::vector<double>& out, std::vector<int32_t>& info) {
+static int read_outputs(Batch& B, std::vector<double>& out, std::vector<int32_t>& info, int* err_flag = nullptr) {
   out.resize((size_t)B.n * SLOT_NOUT);
   info.resize((size_t)B.n * 2);
   for (int i = 0; i < B.n; ++i) {
     cudaMemcpyAsync(&out[(size_t)i * SLOT_NOUT], B.h[i].out, SLOT_NOUT * 8, cudaMemcpyDeviceToHost, B.st);
     cudaMemcpyAsync(&info[(size_t)i * 2], B.h[i].info, 8, cudaMemcpyDeviceToHost, B.st);
   }
+  int e = 0;
+  if (B.err) cudaMemcpyAsync(&e, B.err, 4, cudaMemcpyDeviceToHost, B.st);
   INLA_CUDA_TRY(cudaStreamSynchronize(B.st));
-  return INLA_OK;
+  INLA_CUDA_TRY(cudaGetLastError());
+  if (err_flag) *err_flag = e;
+  return e ? INLA_E_TIMEOUT : INLA_OK;
 }
 
 static void fail_slot(Batch& B, std::vector<int>& status, int i, int code) {
@@ -173,6 +238,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   std::vector<int32_t> info;
   status.assign(NB, INLA_OK);
   iters.assign(NB, 0);
+  if (B.err) cudaMemsetAsync(B.err, 0, 4, B.st);
   for (int i = 0; i < NB; ++i) {
     cudaMemsetAsync(B.h[i].out, 0, SLOT_NOUT * 8, B.st);
     const int32_t init_info[2] = {0, INT_MAX};
@@ -183,14 +249,11 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   // ---------------- prior precision ----------------
   launch_theta_prior(B.d_slots, NB, B.st);
   for (int i = 0; i < NB; ++i) cudaMemsetAsync(B.h[i].Qp, 0, (size_t)B.h[i].n_pad * B.h[i].n_pad * 8, B.st);
-  if (B.max_td > 0) {
-    launch_cov_build(B.d_slots, NB, B.max_td, B.st);
-    potrf(B, SEL_COV);
-    launch_logdet(B.d_slots, NB, SEL_COV, OUT_LOGDET_COV, B.st);
-    trtri(B, SEL_COV, DST_L);
-    launch_lauum_cov(B.d_slots, NB, B.max_td, B.st);
-  }
-  launch_prior_entries(B.d_slots, NB, B.max_entries, B.st);
+  INLA_TRY(debug_check(B.st, "prior start"));
+  if (B.max_td > 0) INLA_TRY(op_prior_dense(B));
+  INLA_TRY(debug_check(B.st, "prior dense"));
+  if (B.mixed) launch_prior_entries_df(B.d_slots, NB, B.max_entries, B.st);
+  else launch_prior_entries(B.d_slots, NB, B.max_entries, B.st);
   launch_mirror_qp(B.d_slots, NB, B.max_t, B.st);
   launch_prior_logdet(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
@@ -200,7 +263,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   // ---------------- Newton iterations ----------------
   launch_zero_vec(B.d_slots, NB, 0, B.max_n, B.st);
   launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
-  launch_qp_gemv(B.d_slots, NB, 0, B.max_n, B.st);
+  op_qp_gemv(B, 0);
   INLA_TRY(read_outputs(B, out, info));
   std::vector<double> f_old(NB);
   for (int i = 0; i < NB; ++i) f_old[i] = objective(*models[i], &out[(size_t)i * SLOT_NOUT]);
@@ -208,31 +271,36 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   int* d_flags = nullptr;
   INLA_CUDA_TRY(cudaMallocAsync((void**)&d_flags, sizeof(int) * NB, B.st));
   std::vector<int> flags(NB, 0);
-  for (int it = 1; it <= o.newton_max; ++it) {
+  int rc = INLA_OK;
+  for (int it = 1; it <= o.newton_max && rc == INLA_OK; ++it) {
     int nact = 0;
     for (int i = 0; i < NB; ++i) nact += B.h[i].active;
     if (nact == 0) break;
     for (int i = 0; i < NB; ++i)
       if (B.h[i].active) iters[i] = it;
     // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction
-    launch_copy_qp_to_l(B.d_slots, NB, B.max_t, B.st);
-    launch_add_pairs(B.d_slots, NB, B.max_pairs, B.st);
+    op_assemble_q(B);
     launch_gradient(B.d_slots, NB, B.max_n, B.st);
-    potrf(B, SEL_L);
+    if ((rc = debug_check(B.st, "newton assemble")) != INLA_OK) break;
+    if ((rc = op_potrf(B, SEL_L)) != INLA_OK) break;
+    if ((rc = debug_check(B.st, "newton potrf")) != INLA_OK) break;
     solve_llt(B, SEL_L, V_G, V_T2, V_G);
+    if ((rc = debug_check(B.st, "newton solve")) != INLA_OK) break;
     launch_newton_xu(B.d_slots, NB, B.max_n, B.st);
     if (B.max_k > 0) {
-      constraint_schur(B);
+      if ((rc = op_schur(B)) != INLA_OK) break;
       launch_cx(B.d_slots, NB, B.max_k, B.st);
       solve_llt(B, SEL_S, V_KV1, V_KV2, V_KV1);
-      launch_z_gemv(B.d_slots, NB, B.max_n, B.st);
+      if (B.mixed) launch_z_gemv_df(B.d_slots, NB, B.max_n, B.st);
+      else launch_z_gemv(B.d_slots, NB, B.max_n, B.st);
       solve_lt(B, SEL_L, V_T2, V_G);
       launch_krige_apply(B.d_slots, NB, B.max_n, B.st);
+      if ((rc = debug_check(B.st, "newton kriging")) != INLA_OK) break;
     }
     launch_eval_lik(B.d_slots, NB, 1, B.max_m, B.st);
-    launch_qp_gemv(B.d_slots, NB, 1, B.max_n, B.st);
+    op_qp_gemv(B, 1);
     launch_step_norm(B.d_slots, NB, B.max_n, B.st);
-    INLA_TRY(read_outputs(B, out, info));
+    if ((rc = read_outputs(B, out, info)) != INLA_OK) break;
     for (int i = 0; i < NB; ++i)
       if (B.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(B, status, i, INLA_E_NOT_SPD);
     // step halving while the objective decreases
@@ -248,10 +316,11 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
       cudaMemcpyAsync(d_flags, flags.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, B.st);
       launch_halve(B.d_slots, NB, d_flags, B.max_n, B.st);
       launch_eval_lik(B.d_slots, NB, 1, B.max_m, B.st);
-      launch_qp_gemv(B.d_slots, NB, 1, B.max_n, B.st);
+      op_qp_gemv(B, 1);
       launch_step_norm(B.d_slots, NB, B.max_n, B.st);
-      INLA_TRY(read_outputs(B, out, info));
+      if ((rc = read_outputs(B, out, info)) != INLA_OK) break;
     }
+    if (rc != INLA_OK) break;
     launch_accept(B.d_slots, NB, B.max_n, B.st);
     for (int i = 0; i < NB; ++i) {
       if (!B.h[i].active) continue;
@@ -269,6 +338,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
     sync_active(B);
   }
   cudaFreeAsync(d_flags, B.st);
+  if (rc != INLA_OK) return rc;
   for (int i = 0; i < NB; ++i) {
     if (status[i] == INLA_OK && !converged[i]) status[i] = INLA_E_NO_CONVERGENCE;
     B.h[i].active = status[i] == INLA_OK;
@@ -276,25 +346,18 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   sync_active(B);
   // ---------------- at the mode ----------------
   launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
-  launch_qp_gemv(B.d_slots, NB, 0, B.max_n, B.st);
-  launch_copy_qp_to_l(B.d_slots, NB, B.max_t, B.st);
-  launch_add_pairs(B.d_slots, NB, B.max_pairs, B.st);
-  potrf(B, SEL_L);
-  launch_logdet(B.d_slots, NB, SEL_L, OUT_LOGDET_Q, B.st);
+  op_qp_gemv(B, 0);
+  op_assemble_q(B);
+  INLA_TRY(op_potrf(B, SEL_L));
+  op_logdet(B, SEL_L, OUT_LOGDET_Q);
+  INLA_TRY(debug_check(B.st, "final potrf"));
   if (B.max_k > 0) {
-    constraint_schur(B);
-    launch_logdet(B.d_slots, NB, SEL_S, OUT_LOGDET_S, B.st);
+    INLA_TRY(op_schur(B));
+    op_logdet(B, SEL_S, OUT_LOGDET_S);
   }
-  if (want_var) {
-    trtri(B, SEL_L, DST_WK);
-    launch_colsumsq_wk(B.d_slots, NB, B.max_t, B.st);
-    if (B.max_k > 0) {
-      launch_zt_w(B.d_slots, NB, B.max_tk, B.max_t, B.st);
-      for (int kt = 0; kt < B.max_tk; ++kt) launch_fwd_s_rhs_step(B.d_slots, NB, kt, B.max_tk, B.max_t, B.st);
-      launch_colsumsq_gt(B.d_slots, NB, B.max_tk, B.max_t, B.st);
-      launch_var_finish(B.d_slots, NB, B.max_n, B.st);
-    }
-  }
+  INLA_TRY(debug_check(B.st, "final schur"));
+  if (want_var) INLA_TRY(op_variances(B));
+  INLA_TRY(debug_check(B.st, "final variances"));
   launch_assemble(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
   for (int i = 0; i < NB; ++i)
@@ -302,7 +365,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   return INLA_OK;
 }
 
-// log-determinant of a host SPD matrix (k_pad x k_pad, k_pad a multiple of TB) on the device
+// log-determinant of a host SPD matrix (k x k, k a multiple of TB) on the device, FP64
 int logdet_spd_device(const std::vector<double>& Mhost, int k, double* result) {
   std::lock_guard<std::mutex> lock(g_mutex);
   Slot s;
@@ -330,7 +393,8 @@ int logdet_spd_device(const std::vector<double>& Mhost, int k, double* result) {
     B.n = 1;
     B.max_tk = k / TB;
     B.st = 0;
-    potrf(B, SEL_S);
+    B.mixed = false;
+    potrf64(B, SEL_S);
     launch_logdet(d_slot, 1, SEL_S, OUT_LOGDET_S, 0);
     double o[SLOT_NOUT];
     int32_t inf[2];
@@ -346,6 +410,98 @@ int logdet_spd_device(const std::vector<double>& Mhost, int k, double* result) {
   return st;
 }
 
+// -------------------------------------------------------------------------------------
+// one group of points with identical model shapes
+// -------------------------------------------------------------------------------------
+struct Layout {
+  int np, ndp, kp, m, S;
+  bool mixed, want_var;
+};
+
+// carve the group's workspace (uniform strides); returns the bytes used
+static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vector<Slot>& h) {
+  const size_t np = L.np, kp = L.kp, ndp = std::max(L.ndp, 1), m = std::max(L.m, 1);
+  B.np = L.np;
+  B.ndp = L.ndp;
+  B.kp = L.kp;
+  B.mat_stride = (int64_t)np * np;
+  B.z_stride = (int64_t)np * kp;
+  B.s_stride = (int64_t)kp * kp;
+  B.linv_stride = (int64_t)np * TB;
+  B.wd_stride = (int64_t)ndp * TB;
+  B.slinv_stride = (int64_t)kp * TB;
+  double* Qp = cv.take<double>(G * np * np);
+  double* Lm = cv.take<double>(G * np * np);
+  double* Wk = cv.take<double>(G * np * np);
+  double* Linv = cv.take<double>(G * np * TB);
+  double* Wd = cv.take<double>(G * ndp * TB);
+  double *Z = nullptr, *S = nullptr, *SLinv = nullptr, *kv1 = nullptr, *kv2 = nullptr;
+  if (kp) {
+    Z = cv.take<double>(G * np * kp);
+    S = cv.take<double>(G * kp * kp);
+    SLinv = cv.take<double>(G * kp * TB);
+    kv1 = cv.take<double>(G * kp);
+    kv2 = cv.take<double>(G * kp);
+  }
+  double* vecs = cv.take<double>(G * np * 6);
+  double* mvecs = cv.take<double>(G * m * 2);
+  double* red = cv.take<double>(G * 256);
+  double* outs = cv.take<double>(G * SLOT_NOUT);
+  int32_t* infos = cv.take<int32_t>(G * 2);
+  B.mixed = L.mixed;
+  B.S = L.S;
+  B.PA = B.PB = B.PBIG = nullptr;
+  B.EA = B.EB = B.EBIG = nullptr;
+  B.err = cv.take<int32_t>(1);
+  if (L.mixed) {
+    const int64_t nch = (int64_t)(np + OZ_CHUNK - 1) / OZ_CHUNK;
+    B.pa_cap = (int64_t)L.S * np * std::max<size_t>(256, kp);
+    B.pb_cap = (int64_t)L.S * np * 256;
+    B.pbig_cap = (int64_t)L.S * np * np;
+    B.ea_cap = nch * (int64_t)std::max<size_t>(np, kp) + np;
+    B.eb_cap = nch * (int64_t)np + np;
+    B.ebig_cap = nch * (int64_t)np;
+    B.PA = cv.take<uint16_t>(G * B.pa_cap);
+    B.PB = cv.take<uint16_t>(G * B.pb_cap);
+    B.PBIG = cv.take<uint16_t>(G * B.pbig_cap);
+    B.EA = cv.take<int32_t>(G * B.ea_cap);
+    B.EB = cv.take<int32_t>(G * B.eb_cap);
+    B.EBIG = cv.take<int32_t>(G * B.ebig_cap);
+  }
+  h.resize(G);
+  for (int i = 0; i < G; ++i) {
+    Slot& s = h[i];
+    std::memset(&s, 0, sizeof(s));
+    s.Qp = Qp ? Qp + i * np * np : nullptr;
+    s.L = Lm ? Lm + i * np * np : nullptr;
+    s.Wk = Wk ? Wk + i * np * np : nullptr;
+    s.Linv = Linv ? Linv + i * np * TB : nullptr;
+    s.Wd = Wd ? Wd + i * ndp * TB : nullptr;
+    if (kp && Z) {
+      s.Z = Z + i * np * kp;
+      s.S = S + i * kp * kp;
+      s.SLinv = SLinv + i * kp * TB;
+      s.kv1 = kv1 + i * kp;
+      s.kv2 = kv2 + i * kp;
+    }
+    if (vecs) {
+      double* v = vecs + i * np * 6;
+      s.x = v;
+      s.xn = v + np;
+      s.g = v + 2 * np;
+      s.t1 = v + 3 * np;
+      s.t2 = v + 4 * np;
+      s.vd = v + 5 * np;
+      s.eta = mvecs + i * m * 2;
+      s.w = s.eta + m;
+      s.red = red + i * 256;
+      s.out = outs + i * SLOT_NOUT;
+      s.info = infos + i * 2;
+    }
+  }
+  return cv.off;
+}
+
 static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int32_t* model_of_theta,
                            const double* thetas, int32_t B_, const inla_opts* opts_in, double* log_post,
                            int32_t* status_out, double* const* x_hat, double* const* var,
@@ -357,16 +513,20 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   if (opts_in) o = *opts_in;
   if (o.newton_tol <= 0) o.newton_tol = 1e-8;
   if (o.newton_max <= 0) o.newton_max = 50;
-  if (o.precision != INLA_FP64) return INLA_E_UNSUPPORTED;
+  if (o.spin_limit <= 0) o.spin_limit = (int64_t)1 << 26;
+  if (o.precision != INLA_FP64 && o.precision != INLA_MIXED) return INLA_E_BADARG;
+  const bool mixed = o.precision == INLA_MIXED;
+  const int S = mixed ? (o.slices == 0 ? 4 : o.slices) : 0;
+  if (mixed && (S < 2 || S > OZ_MAX_S)) return INLA_E_BADARG;
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
   const bool want_var = var != nullptr;
-  std::vector<const ModelDev*> mlist(B_);
   int theta_dim = -1;
+  std::vector<int> mi_of(B_);
   for (int b = 0; b < B_; ++b) {
     const int mi = model_of_theta ? model_of_theta[b] : 0;
     if (mi < 0 || mi >= nmodels || !models[mi]) return INLA_E_BADARG;
-    mlist[b] = &models[mi]->d;
+    mi_of[b] = mi;
     if (theta_dim >= 0 && theta_dim != models[mi]->d.theta_dim) return INLA_E_BADARG;
     theta_dim = models[mi]->d.theta_dim;
   }
@@ -375,116 +535,120 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   int device = 0;
   INLA_CUDA_TRY(cudaGetDevice(&device));
   std::lock_guard<std::mutex> lock(g_mutex);
-  // workspace: all slots, the model structs, the slot table, permutations
-  size_t bytes = 0;
-  for (int b = 0; b < B_; ++b) bytes += slot_bytes(*mlist[b], want_var);
-  bytes += sizeof(Slot) * B_ + 4096;
-  int max_n_pad = 0;
-  for (int mi = 0; mi < nmodels; ++mi) {
-    bytes += sizeof(ModelDev) + (size_t)models[mi]->d.n * sizeof(int32_t) + 512;
-    max_n_pad = std::max(max_n_pad, models[mi]->d.n_pad);
+  // group the points by model shape
+  std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> groups;
+  for (int b = 0; b < B_; ++b) {
+    const ModelDev& d = models[mi_of[b]]->d;
+    groups[std::make_tuple(d.n_pad, d.nd_pad, d.k_pad, d.m, d.nd, d.nd_off)].push_back(b);
   }
-  bytes += (size_t)max_n_pad * sizeof(double) + 512;
+  // workspace: the largest group, plus model structs, permutations, gather buffer
+  size_t need = 0;
+  for (auto& kv : groups) {
+    const ModelDev& d = models[mi_of[kv.second[0]]]->d;
+    Layout L{d.n_pad, d.nd_pad, d.k_pad, d.m, S, mixed, want_var};
+    Carve cv(nullptr);
+    Batch Bt;
+    std::vector<Slot> h;
+    size_t b = carve_group(cv, L, (int)kv.second.size(), Bt, h);
+    b += sizeof(Slot) * kv.second.size() + 4096;
+    need = std::max(need, b);
+  }
+  int max_np = 0;
+  size_t extra = 0;
+  for (int mi = 0; mi < nmodels; ++mi) {
+    extra += sizeof(ModelDev) + (size_t)models[mi]->d.n * sizeof(int32_t) + 1024;
+    max_np = std::max(max_np, models[mi]->d.n_pad);
+  }
+  extra += (size_t)max_np * sizeof(double) + 1024;
+  need = (size_t)round_up((int64_t)need, 256);  // the fixed part starts on a 256-byte boundary
+  const size_t bytes = need + extra;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  if (bytes > (size_t)(0.95 * (double)(free_b + (g_arena.device == device ? g_arena.size : 0))))
-    return INLA_E_NOMEM;
+  if (bytes > (size_t)(0.95 * (double)(free_b + (g_arena.device == device ? g_arena.size : 0)))) return INLA_E_NOMEM;
   INLA_TRY(arena_reserve(bytes, device));
-  Carve cv(g_arena.base);
-  Batch Bt;
-  Bt.n = B_;
-  Bt.st = st;
-  Bt.h.resize(B_);
-  Bt.max_t = Bt.max_td = Bt.max_tk = Bt.max_m = Bt.max_n = Bt.max_k = 0;
-  Bt.max_entries = Bt.max_pairs = 0;
+  // fixed part at the end of the arena: model structs, permutations, gather buffer
+  Carve cfix(static_cast<char*>(g_arena.base) + need);
   std::vector<ModelDev*> d_models(nmodels, nullptr);
-  for (int mi = 0; mi < nmodels; ++mi) {
-    d_models[mi] = cv.take<ModelDev>(1);
-    cudaMemcpyAsync(d_models[mi], &models[mi]->d, sizeof(ModelDev), cudaMemcpyHostToDevice, st);
-  }
-  for (int b = 0; b < B_; ++b) {
-    const int mi = model_of_theta ? model_of_theta[b] : 0;
-    const ModelDev& d = *mlist[b];
-    Slot& s = Bt.h[b];
-    std::memset(&s, 0, sizeof(s));
-    const size_t np = d.n_pad, kp = d.k_pad;
-    s.Qp = cv.take<double>(np * np);
-    s.L = cv.take<double>(np * np);
-    s.Wk = cv.take<double>(np * np);
-    s.Linv = cv.take<double>(np * TB);
-    s.Wd = cv.take<double>(std::max<size_t>(d.nd_pad, 1) * TB);
-    if (kp) {
-      s.Z = cv.take<double>(np * kp);
-      s.S = cv.take<double>(kp * kp);
-      s.SLinv = cv.take<double>(kp * TB);
-      s.kv1 = cv.take<double>(kp);
-      s.kv2 = cv.take<double>(kp);
-    }
-    s.x = cv.take<double>(np);
-    s.xn = cv.take<double>(np);
-    s.g = cv.take<double>(np);
-    s.t1 = cv.take<double>(np);
-    s.t2 = cv.take<double>(np);
-    s.eta = cv.take<double>(std::max<size_t>(d.m, 1));
-    s.w = cv.take<double>(std::max<size_t>(d.m, 1));
-    s.red = cv.take<double>(256);
-    s.out = cv.take<double>(SLOT_NOUT);
-    s.info = cv.take<int32_t>(2);
-    s.md = d_models[mi];
-    s.n_pad = d.n_pad;
-    s.n = d.n;
-    s.m = d.m;
-    s.k = d.k;
-    s.k_pad = d.k_pad;
-    s.nd = d.nd;
-    s.nd_pad = d.nd_pad;
-    s.active = 1;
-    for (int t = 0; t < theta_dim; ++t) s.theta[t] = thetas[(size_t)b * theta_dim + t];
-    Bt.max_t = std::max(Bt.max_t, d.n_pad / TB);
-    Bt.max_td = std::max(Bt.max_td, d.nd_pad / TB);
-    Bt.max_tk = std::max(Bt.max_tk, d.k_pad / TB);
-    Bt.max_m = std::max(Bt.max_m, d.m);
-    Bt.max_n = std::max(Bt.max_n, d.n_pad);
-    Bt.max_k = std::max(Bt.max_k, d.k_pad);
-    Bt.max_entries = std::max(Bt.max_entries, d.nentries);
-    Bt.max_pairs = std::max(Bt.max_pairs, d.npairs);
-  }
-  Bt.d_slots = cv.take<Slot>(B_);
-  // permutations (internal -> original gather), one per model
   std::vector<int32_t*> d_perm(nmodels, nullptr);
   for (int mi = 0; mi < nmodels; ++mi) {
-    d_perm[mi] = cv.take<int32_t>(models[mi]->d.n);
+    d_models[mi] = cfix.take<ModelDev>(1);
+    cudaMemcpyAsync(d_models[mi], &models[mi]->d, sizeof(ModelDev), cudaMemcpyHostToDevice, st);
+    d_perm[mi] = cfix.take<int32_t>(models[mi]->d.n);
     cudaMemcpyAsync(d_perm[mi], models[mi]->perm.data(), sizeof(int32_t) * models[mi]->d.n, cudaMemcpyHostToDevice, st);
   }
-  double* d_gather = cv.take<double>(Bt.max_n);
-  if (cv.off > g_arena.size) return INLA_E_NOMEM;
-  std::vector<int> status, iters;
-  int rc = run_batch(Bt, mlist, o, want_var, status, iters);
-  if (rc != INLA_OK) return rc;
-  std::vector<double> out;
-  std::vector<int32_t> info;
-  // outputs
-  for (int b = 0; b < B_; ++b) Bt.h[b].active = 1;
-  INLA_TRY(read_outputs(Bt, out, info));
-  for (int b = 0; b < B_; ++b) {
-    const int mi = model_of_theta ? model_of_theta[b] : 0;
-    const int n = models[mi]->d.n;
-    status_out[b] = status[b];
-    if (iters_out) iters_out[b] = iters[b];
-    log_post[b] =status[b] == INLA_OK ? out[(size_t)b * SLOT_NOUT + OUT_LOGPOST] : NAN;
-    const double* srcs[2] = {Bt.h[b].x, Bt.h[b].t1};
-    double* const* dsts[2] = {x_hat, var};
-    for (int q = 0; q < 2; ++q) {
-      if (!dsts[q] || !dsts[q][b]) continue;
-      if (dev_out) {
-        launch_gather(dsts[q][b], srcs[q], d_perm[mi], n, st);
-      } else {
-        launch_gather(d_gather, srcs[q], d_perm[mi], n, st);
-        cudaMemcpyAsync(dsts[q][b], d_gather, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  double* d_gather = cfix.take<double>(max_np);
+  for (auto& kv : groups) {
+    const std::vector<int>& idx = kv.second;
+    const int G = (int)idx.size();
+    const ModelDev& d0 = models[mi_of[idx[0]]]->d;
+    Layout L{d0.n_pad, d0.nd_pad, d0.k_pad, d0.m, S, mixed, want_var};
+    Carve cv(g_arena.base);
+    Batch Bt;
+    carve_group(cv, L, G, Bt, Bt.h);
+    Bt.d_slots = cv.take<Slot>(G);
+    Bt.n = G;
+    Bt.st = st;
+    Bt.spin_limit = o.spin_limit;
+    Bt.max_t = d0.n_pad / TB;
+    Bt.max_td = d0.nd_pad / TB;
+    Bt.max_tk = d0.k_pad / TB;
+    Bt.max_m = d0.m;
+    Bt.max_n = d0.n_pad;
+    Bt.max_k = d0.k_pad;
+    Bt.max_entries = 0;
+    Bt.max_pairs = 0;
+    std::vector<const ModelDev*> mlist(G);
+    for (int g = 0; g < G; ++g) {
+      const int b = idx[g];
+      const ModelDev& d = models[mi_of[b]]->d;
+      mlist[g] = &d;
+      Slot& s = Bt.h[g];
+      s.md = d_models[mi_of[b]];
+      s.n_pad = d.n_pad;
+      s.n = d.n;
+      s.m = d.m;
+      s.k = d.k;
+      s.k_pad = d.k_pad;
+      s.nd = d.nd;
+      s.nd_pad = d.nd_pad;
+      s.nd_off = d.nd_off;
+      s.active = 1;
+      for (int t = 0; t < theta_dim; ++t) s.theta[t] = thetas[(size_t)b * theta_dim + t];
+      Bt.max_entries = std::max(Bt.max_entries, d.nentries);
+      Bt.max_pairs = std::max(Bt.max_pairs, d.npairs);
+    }
+    if (mixed) {
+      for (int g = 1; g < G; ++g)
+        if (Bt.h[g].nd != Bt.h[0].nd) return INLA_E_UNSUPPORTED;
+    }
+    std::vector<int> status, iters;
+    int rc = run_batch(Bt, mlist, o, want_var, status, iters);
+    if (rc != INLA_OK) return rc;
+    std::vector<double> out;
+    std::vector<int32_t> info;
+    for (int g = 0; g < G; ++g) Bt.h[g].active = 1;
+    INLA_TRY(read_outputs(Bt, out, info));
+    for (int g = 0; g < G; ++g) {
+      const int b = idx[g];
+      const int mi = mi_of[b];
+      const int n = models[mi]->d.n;
+      status_out[b] = status[g];
+      if (iters_out) iters_out[b] = iters[g];
+      log_post[b] = status[g] == INLA_OK ? out[(size_t)g * SLOT_NOUT + OUT_LOGPOST] : NAN;
+      const double* srcs[2] = {Bt.h[g].x, Bt.h[g].t1};
+      double* const* dsts[2] = {x_hat, var};
+      for (int q = 0; q < 2; ++q) {
+        if (!dsts[q] || !dsts[q][b]) continue;
+        if (dev_out) {
+          launch_gather(dsts[q][b], srcs[q], d_perm[mi], n, st);
+        } else {
+          launch_gather(d_gather, srcs[q], d_perm[mi], n, st);
+          cudaMemcpyAsync(dsts[q][b], d_gather, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        }
       }
     }
+    INLA_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  INLA_CUDA_TRY(cudaStreamSynchronize(st));
   INLA_CUDA_TRY(cudaGetLastError());
   return INLA_OK;
 }
@@ -493,7 +657,7 @@ __global__ void k_gather(double* dst, const double* src, const int32_t* perm, in
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[perm[i]];
 }
 void launch_gather(double* dst, const double* src, const int32_t* perm, int n, cudaStream_t st) {
-  k_gather<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(dst, src, perm, n);
+  count_launch(), k_gather<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(dst, src, perm, n);
 }
 
 }  // namespace inla
@@ -546,6 +710,14 @@ extern "C" int inla_marginals(inla_model* model, const double* theta, const inla
   int rc = inla_eval_batch(ms, 1, nullptr, theta, 1, opts, &lp, &st, xs, vs);
   if (rc != INLA_OK) return rc;
   return st;
+}
+
+extern "C" const char* inla_test_debug_site(void) { return g_debug_site; }
+
+extern "C" int64_t inla_test_launch_count(void) {
+  const int64_t n = g_kernel_launches;
+  g_kernel_launches = 0;
+  return n;
 }
 
 extern "C" const char* inla_status_string(int s) {

@@ -1,0 +1,215 @@
+// Blocked dense routines of the mixed path.  Matrices are double-float; every product with a
+// non-trivial K runs on the Ozaki-split tensor-core GEMM; the 64 x 64 diagonal tiles are
+// factored and inverted in FP64.  Two-level blocking: 256-wide outer panels keep the
+// trailing updates' K at one exact accumulation chunk (and C traffic at n^3 / (3 * 256)
+// element updates per factorisation), 64-wide inner steps keep the FP64 work small.
+#include "df64.cuh"
+#include "mixed.h"
+
+namespace inla {
+
+namespace {
+
+constexpr int NB = 256;   // outer block
+constexpr int IB = TB;    // inner block (64)
+
+struct MRef {
+  float2* base;       // slot-0 matrix
+  int64_t stride;     // elements between slots
+  int n, ld;
+  double* linv;       // slot-0 diagonal-tile inverses (n x 64 FP64)
+  int64_t linv_stride;
+  int sel;
+};
+
+MRef mref(const Batch& B, int sel) {
+  const Slot& s = B.h[0];
+  if (sel == SEL_L) return MRef{reinterpret_cast<float2*>(s.L), B.mat_stride, B.np, B.np, s.Linv, B.linv_stride, sel};
+  if (sel == SEL_COV) return MRef{reinterpret_cast<float2*>(s.Wk), B.mat_stride, B.ndp, B.np, s.Wd, B.wd_stride, sel};
+  return MRef{reinterpret_cast<float2*>(s.S), B.s_stride, B.kp, B.kp, s.SLinv, B.slinv_stride, sel};
+}
+
+OzOperand operand(uint16_t* planes, int32_t* exps, int rows, int K) {
+  OzOperand o;
+  o.planes = planes;
+  o.exps = exps;
+  o.rows = rows;
+  o.K = K;
+  o.ld_k = (int)round_up(K, OZ_BK);
+  o.plane_stride = (int64_t)rows * o.ld_k;
+  o.exp_chunk_stride = rows;
+  o.exp_slot_stride = (int64_t)((K + OZ_CHUNK - 1) / OZ_CHUNK) * rows;
+  return o;
+}
+
+OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, int N, int K, float alpha, float beta) {
+  OzArgs a;
+  memset(&a, 0, sizeof(a));
+  a.C = C;
+  a.C_slot_stride = c_stride;
+  a.ldc = ldc;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.S = B.S;
+  a.spin_limit = B.spin_limit;
+  a.err = B.err;
+  return a;
+}
+
+}  // namespace
+
+// In-place Cholesky of the matrix selected by `sel` (lower triangle), every slot.
+int mixed_potrf(Batch& B, int sel) {
+  const MRef M = mref(B, sel);
+  const int n = M.n, S = B.S;
+  for (int K0 = 0; K0 < n; K0 += NB) {
+    const int kend = std::min(K0 + NB, n);
+    for (int j0 = K0; j0 < kend; j0 += IB) {
+      launch_potrf_diag_df(B.d_slots, B.n, sel, j0 / IB, B.st);
+      const int R = n - j0 - IB;
+      if (R <= 0) continue;
+      float2* panel = M.base + (int64_t)(j0 + IB) * M.ld + j0;
+      // X = A_panel Linv^T
+      OzOperand pa = operand(B.PA, B.EA, R, IB);
+      OzOperand pb = operand(B.PB, B.EB, IB, IB);
+      oz_slice_df(M.base, M.stride, M.ld, j0 + IB, j0, R, IB, false, pa, S, B.n, B.st);
+      oz_slice_f64(M.linv + (int64_t)(j0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB, false, pb, S, B.n, B.st);
+      OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
+      INLA_TRY(oz_gemm(pa, pb, a, B.n, B.st));
+      // rest of the 256-wide panel: A[j0+64:, j0+64:kend] -= X X_top^T
+      const int w = kend - (j0 + IB);
+      if (w > 0) {
+        OzOperand px = operand(B.PA, B.EA, R, IB);
+        oz_slice_df(M.base, M.stride, M.ld, j0 + IB, j0, R, IB, false, px, S, B.n, B.st);
+        OzOperand pxt = px;
+        pxt.rows = w;  // the first w rows of X, same planes
+        OzArgs u = gemm_args(B, M.base + (int64_t)(j0 + IB) * M.ld + (j0 + IB), M.stride, M.ld, R, w, IB, 1.f, -1.f);
+        INLA_TRY(oz_gemm(px, pxt, u, B.n, B.st));
+      }
+    }
+    const int R2 = n - kend;
+    if (R2 > 0) {
+      OzOperand pp = operand(B.PA, B.EA, R2, kend - K0);
+      oz_slice_df(M.base, M.stride, M.ld, kend, K0, R2, kend - K0, false, pp, S, B.n, B.st);
+      OzArgs a = gemm_args(B, M.base + (int64_t)kend * M.ld + kend, M.stride, M.ld, R2, R2, kend - K0, 1.f, -1.f);
+      a.lower = 1;
+      INLA_TRY(oz_gemm(pp, pp, a, B.n, B.st));
+    }
+  }
+  return INLA_OK;
+}
+
+// X <- F^-1 X (forward substitution, F lower-triangular factor selected by `fsel`), X with
+// `nrows` = F.n rows and `ncols` columns (leading dimension ldx).  identity: X = I on entry,
+// so block row K only has nonzero columns [0, end of block K).
+static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, int ncols, bool identity) {
+  const MRef F = mref(B, fsel);
+  const int n = F.n, S = B.S;
+  for (int K0 = 0; K0 < n; K0 += NB) {
+    const int kend = std::min(K0 + NB, n);
+    const int nc = identity ? std::min(kend, ncols) : ncols;
+    for (int j0 = K0; j0 < kend; j0 += IB) {
+      // X[j0 tile, 0:nc] = Linv_j X[j0 tile, 0:nc]
+      OzOperand pl = operand(B.PA, B.EA, IB, IB);
+      OzOperand px = operand(B.PB, B.EB, nc, IB);
+      oz_slice_f64(F.linv + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB, false, pl, S, B.n, B.st);
+      oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px, S, B.n, B.st);
+      OzArgs a = gemm_args(B, X + (int64_t)j0 * ldx, x_stride, ldx, IB, nc, IB, 0.f, 1.f);
+      INLA_TRY(oz_gemm(pl, px, a, B.n, B.st));
+      const int r_hi = kend;
+      if (j0 + IB < r_hi) {
+        const int R = r_hi - j0 - IB;
+        OzOperand pf = operand(B.PA, B.EA, R, IB);
+        OzOperand px2 = operand(B.PB, B.EB, nc, IB);
+        oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, B.st);
+        oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px2, S, B.n, B.st);
+        OzArgs u = gemm_args(B, X + (int64_t)(j0 + IB) * ldx, x_stride, ldx, R, nc, IB, 1.f, -1.f);
+        INLA_TRY(oz_gemm(pf, px2, u, B.n, B.st));
+      }
+    }
+    const int R = n - kend;
+    if (R > 0) {
+      OzOperand pf = operand(B.PA, B.EA, R, kend - K0);
+      OzOperand px = operand(B.PB, B.EB, nc, kend - K0);
+      oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, B.st);
+      oz_slice_df(X, x_stride, ldx, K0, 0, nc, kend - K0, true, px, S, B.n, B.st);
+      OzArgs u = gemm_args(B, X + (int64_t)kend * ldx, x_stride, ldx, R, nc, kend - K0, 1.f, -1.f);
+      INLA_TRY(oz_gemm(pf, px, u, B.n, B.st));
+    }
+  }
+  return INLA_OK;
+}
+
+// W = F^-1 (lower), written into Wk (into_wk) or into L
+int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
+  const MRef F = mref(B, sel);
+  const Slot& s0 = B.h[0];
+  float2* W = reinterpret_cast<float2*>(into_wk ? s0.Wk : s0.L);
+  for (int i = 0; i < B.n; ++i)
+    cudaMemsetAsync(into_wk ? B.h[i].Wk : B.h[i].L, 0, (size_t)B.mat_stride * 8, B.st);
+  launch_diag_ones_df(W, B.mat_stride, B.np, F.n, B.n, B.st);
+  return trsm_left(B, sel, W, B.mat_stride, B.np, F.n, true);
+}
+
+// Q_p[0:nd, 0:nd] = W^T W with W = L_Sigma^-1 held in L (lower)
+int mixed_lauum_cov(Batch& B) {
+  const Slot& s0 = B.h[0];
+  const int ndp = B.ndp, nd = s0.nd, S = B.S;
+  OzOperand pw = operand(B.PBIG, B.EBIG, ndp, ndp);
+  oz_slice_df(reinterpret_cast<float2*>(s0.L), B.mat_stride, B.np, 0, 0, ndp, ndp, true, pw, S, B.n, B.st);
+  float2* C = reinterpret_cast<float2*>(s0.Qp) + (int64_t)s0.nd_off * B.np + s0.nd_off;
+  OzArgs a = gemm_args(B, C, B.mat_stride, B.np, nd, nd, ndp, 0.f, 1.f);
+  a.lower = 1;
+  a.k_mode = 1;
+  return oz_gemm(pw, pw, a, B.n, B.st);
+}
+
+// Z = L^-1 C^T ; S = Z^T Z (identity on the padding) ; factor S
+int mixed_schur(Batch& B) {
+  const Slot& s0 = B.h[0];
+  const int S = B.S;
+  for (int i = 0; i < B.n; ++i) cudaMemsetAsync(B.h[i].Z, 0, (size_t)B.z_stride * 8, B.st);
+  launch_ct_fill_df(B.d_slots, B.n, B.kp, B.st);
+  float2* Z = reinterpret_cast<float2*>(s0.Z);
+  INLA_TRY(trsm_left(B, SEL_L, Z, B.z_stride, B.kp, B.kp, false));
+  OzOperand pz = operand(B.PA, B.EA, B.kp, B.np);
+  oz_slice_df(Z, B.z_stride, B.kp, 0, 0, B.kp, B.np, true, pz, S, B.n, B.st);
+  OzArgs a = gemm_args(B, reinterpret_cast<float2*>(s0.S), B.s_stride, B.kp, B.kp, B.kp, B.np, 0.f, 1.f);
+  a.lower = 1;
+  INLA_TRY(oz_gemm(pz, pz, a, B.n, B.st));
+  launch_s_pad_identity(B.d_slots, B.n, B.kp, B.st);
+  return mixed_potrf(B, SEL_S);
+}
+
+// t2 = colsumsq(L_S^-1 Z^T W), W = Q*^-1 factor inverse in Wk; uses L as scratch
+int mixed_var_constraint(Batch& B) {
+  const Slot& s0 = B.h[0];
+  const int S = B.S;
+  float2* Z = reinterpret_cast<float2*>(s0.Z);
+  float2* W = reinterpret_cast<float2*>(s0.Wk);
+  float2* G = reinterpret_cast<float2*>(s0.L);
+  OzOperand pz = operand(B.PA, B.EA, B.kp, B.np);
+  oz_slice_df(Z, B.z_stride, B.kp, 0, 0, B.kp, B.np, true, pz, S, B.n, B.st);
+  OzOperand pw = operand(B.PBIG, B.EBIG, B.np, B.np);
+  oz_slice_df(W, B.mat_stride, B.np, 0, 0, B.np, B.np, true, pw, S, B.n, B.st);
+  OzArgs a = gemm_args(B, G, B.mat_stride, B.np, B.kp, B.np, B.np, 0.f, 1.f);
+  a.k_mode = 2;
+  INLA_TRY(oz_gemm(pz, pw, a, B.n, B.st));
+  INLA_TRY(trsm_left(B, SEL_S, G, B.mat_stride, B.np, B.np, false));
+  launch_colsumsq_gt_df(B.d_slots, B.n, B.np / TB, B.st);
+  return INLA_OK;
+}
+
+__global__ void k_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n) {
+  float2* W = base + blockIdx.y * slot_stride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    W[(int64_t)i * ld + i] = make_float2(1.f, 0.f);
+}
+void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st) {
+  count_launch(), k_diag_ones_df<<<dim3(std::min(1024, (n + 255) / 256), nslots), 256, 0, st>>>(base, slot_stride, ld, n);
+}
+
+}  // namespace inla

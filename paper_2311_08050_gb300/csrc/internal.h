@@ -49,6 +49,7 @@ struct KronLogdet {
 // Device-resident, theta-independent model data.
 struct ModelDev {
   int32_t n, n_pad, m, k, k_pad, nd, nd_pad;   // nd: dense block size (0 if none)
+  int32_t nd_off;                              // internal offset of the dense block
   int32_t likelihood;
   double lik_prec;
   int32_t theta_dim;
@@ -74,6 +75,9 @@ struct ModelDev {
   int32_t n_iid; int32_t iid_theta[MAX_KRON]; int32_t iid_size[MAX_KRON];
   // constraints (k x n_pad), internal columns
   int64_t *C_rowptr; int32_t *C_col; double *C_val;
+  int64_t ncct;            // entries of C^T C (lower), value in PriorEntry::a
+  PriorEntry *cct;
+  double gamma_c;          // weight of C^T C added to Q* in the constrained solves
   // theta prior
   int32_t prior_kind[MAX_THETA];
   double prior_a[MAX_THETA], prior_b[MAX_THETA];
@@ -103,14 +107,15 @@ struct Slot {
   double *Wd;     // nd_pad x TB: inverses of the diagonal tiles of the covariance factor
   // vectors
   double *x, *xn, *g, *t1, *t2;    // n_pad
+  double *vd;                      // n_pad: double-float copy of a vector (mixed path)
   double *eta, *w;                 // m
   double *kv1, *kv2;               // k_pad
   double *red;                     // reduction scratch (256 doubles)
   double *out;                     // scalar outputs (SLOT_NOUT doubles)
   int32_t *info;                   // [0] status flags, [1] failing pivot
   const ModelDev *md;              // device copy of the model struct
-  int32_t n_pad, n, m, k, k_pad, nd, nd_pad;
-  int32_t active;                  // participates in the current Newton step
+  int32_t n_pad, n, m, k, k_pad, nd, nd_pad, nd_off;
+  int32_t active;                 // participates in the current Newton step
   double theta[MAX_THETA];
 };
 
@@ -132,4 +137,17 @@ enum {
 // info flags
 enum { INFO_NOT_SPD = 1, INFO_TIMEOUT = 2, INFO_NONFINITE = 4 };
 
+}  // namespace inla
+
+namespace inla {
+// Debug mode (environment variable INLA_DEBUG_SYNC=1): every checked site synchronizes the
+// stream and records the first site at which a CUDA error became visible.
+bool debug_sync_enabled();
+int debug_check(cudaStream_t st, const char* site);
+// number of kernels this library has launched (read and reset by inla_test_launch_count)
+extern int64_t g_kernel_launches;
+inline int count_launch() {
+  ++g_kernel_launches;
+  return 0;
+}
 }  // namespace inla

@@ -1,0 +1,105 @@
+// Test hooks (include/inla_testing.h): isolated runs of the mixed-precision building blocks.
+#include <cstring>
+#include <vector>
+#include "../../include/inla_testing.h"
+#include "df64.cuh"
+#include "ozaki.h"
+
+namespace inla {
+
+__global__ void k_f64_to_df(const double* src, float2* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const df v = df_from_double(src[i]);
+    dst[i] = make_float2(v.hi, v.lo);
+  }
+}
+__global__ void k_df_to_f64(const float2* src, double* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i].x + (double)src[i].y;
+}
+
+}  // namespace inla
+
+using namespace inla;
+
+extern "C" int inla_test_ozaki_gemm(const double* A, const double* B, double* C, int32_t M, int32_t N, int32_t K,
+                                    int32_t S, int32_t trans_a, int32_t trans_b, int32_t lower, int32_t k_mode,
+                                    double alpha, double beta) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || (K % OZ_BK) || S < 2 || S > OZ_MAX_S) return INLA_E_BADARG;
+  if (lower && M != N) return INLA_E_BADARG;
+  const int64_t nA = (int64_t)M * K, nB = (int64_t)N * K, nC = (int64_t)M * N;
+  const int ldk = (int)round_up(K, OZ_BK);
+  const int nch = (K + OZ_CHUNK - 1) / OZ_CHUNK;
+  const int rowsA = (int)round_up(M, OZ_BM), rowsB = (int)round_up(N, OZ_BN);
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  float2 *fA = nullptr, *fB = nullptr, *fC = nullptr;
+  uint16_t *pA = nullptr, *pB = nullptr;
+  int32_t *eA = nullptr, *eB = nullptr, *err = nullptr;
+  int rc = INLA_OK;
+  auto fail = [&](int code) { rc = code; };
+  do {
+    if (cudaMalloc(&dA, nA * 8) || cudaMalloc(&dB, nB * 8) || cudaMalloc(&dC, nC * 8) || cudaMalloc(&fA, nA * 8) ||
+        cudaMalloc(&fB, nB * 8) || cudaMalloc(&fC, nC * 8) || cudaMalloc(&pA, (size_t)S * rowsA * ldk * 2) ||
+        cudaMalloc(&pB, (size_t)S * rowsB * ldk * 2) || cudaMalloc(&eA, (size_t)nch * rowsA * 4) ||
+        cudaMalloc(&eB, (size_t)nch * rowsB * 4) || cudaMalloc(&err, 4)) {
+      fail(INLA_E_NOMEM);
+      break;
+    }
+    cudaMemcpy(dA, A, nA * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, B, nB * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dC, C, nC * 8, cudaMemcpyHostToDevice);
+    cudaMemset(err, 0, 4);
+    cudaMemset(pA, 0, (size_t)S * rowsA * ldk * 2);
+    cudaMemset(pB, 0, (size_t)S * rowsB * ldk * 2);
+    k_f64_to_df<<<256, 256>>>(dA, fA, nA);
+    k_f64_to_df<<<256, 256>>>(dB, fB, nB);
+    k_f64_to_df<<<256, 256>>>(dC, fC, nC);
+    OzOperand oa{pA, eA, M, K, ldk, (int64_t)rowsA * ldk, rowsA, 0};
+    OzOperand ob{pB, eB, N, K, ldk, (int64_t)rowsB * ldk, rowsB, 0};
+    // A: M x K (rows) or K x M (transposed source, ld = M)
+    oz_slice_df(fA, 0, trans_a ? M : K, 0, 0, M, K, trans_a != 0, oa, S, 1, 0);
+    oz_slice_df(fB, 0, trans_b ? N : K, 0, 0, N, K, trans_b != 0, ob, S, 1, 0);
+    OzArgs args;
+    std::memset(&args, 0, sizeof(args));
+    args.C = fC;
+    args.ldc = N;
+    args.M = M;
+    args.N = N;
+    args.K = K;
+    args.k_mode = k_mode;
+    args.lower = lower;
+    args.lower_elems = lower;
+    args.alpha = (float)alpha;
+    args.beta = (float)beta;
+    args.S = S;
+    args.spin_limit = (int64_t)1 << 26;
+    args.err = err;
+    rc = oz_gemm(oa, ob, args, 1, 0);
+    if (rc != INLA_OK) break;
+    k_df_to_f64<<<256, 256>>>(fC, dC, nC);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      fail(INLA_E_CUDA);
+      break;
+    }
+    int herr = 0;
+    cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+    if (herr) {
+      fail(INLA_E_TIMEOUT);
+      break;
+    }
+    cudaMemcpy(C, dC, nC * 8, cudaMemcpyDeviceToHost);
+  } while (0);
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  cudaFree(fA);
+  cudaFree(fB);
+  cudaFree(fC);
+  cudaFree(pA);
+  cudaFree(pB);
+  cudaFree(eA);
+  cudaFree(eB);
+  cudaFree(err);
+  if (rc == INLA_E_CUDA) cudaGetLastError();
+  return rc;
+}

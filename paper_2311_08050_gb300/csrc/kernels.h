@@ -51,6 +51,8 @@ void launch_prior_logdet(Slot* slots, int nslots, cudaStream_t st);
 void launch_eval_lik(Slot* slots, int nslots, int which, int max_m, cudaStream_t st);
 // t1 = Q_p v (v = x or xn), OUT_QUAD = v^T t1
 void launch_qp_gemv(Slot* slots, int nslots, int which, int max_n, cudaStream_t st);
+// OUT_QUAD = v^T t1 only
+void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st);
 // g = A^T r - t1   (r held in eta)
 void launch_gradient(Slot* slots, int nslots, int max_n, cudaStream_t st);
 // xn = x + g ; kv1 = C xn (if k > 0)
@@ -72,5 +74,7 @@ void launch_theta_prior(Slot* slots, int nslots, cudaStream_t st);
 // var = t1 - t2 (t2 only with constraints) -> t1
 void launch_var_finish(Slot* slots, int nslots, int max_n, cudaStream_t st);
 void launch_assemble(Slot* slots, int nslots, cudaStream_t st);
+// Q* += gamma_c C^T C (lower) for constrained models
+void launch_add_cct(Slot* slots, int nslots, cudaStream_t st);
 
 }  // namespace inla

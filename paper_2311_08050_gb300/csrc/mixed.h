@@ -1,0 +1,55 @@
+// Mixed-precision path: double-float matrices, Ozaki-split tensor-core GEMMs, FP64 64 x 64
+// diagonal tiles.  Declarations shared by eval.cu, eval_mixed.cu and k_df.cu.
+#pragma once
+#include "kernels.h"
+#include "ozaki.h"
+
+namespace inla {
+
+// ---- k_df.cu launchers ----
+void launch_cov_to_df(Slot* slots, int nslots, int max_td, cudaStream_t st);
+void launch_prior_entries_df(Slot* slots, int nslots, int64_t max_entries, cudaStream_t st);
+void launch_add_pairs_df(Slot* slots, int nslots, int64_t max_pairs, cudaStream_t st);
+void launch_add_cct_df(Slot* slots, int nslots, cudaStream_t st);
+void launch_qp_gemv_df(Slot* slots, int nslots, int which, int max_n, cudaStream_t st);
+void launch_z_gemv_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
+void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st);
+void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st);
+void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st);
+void launch_trsv_fwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t, cudaStream_t st);
+void launch_trsv_bwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, cudaStream_t st);
+void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st);
+void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
+void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
+void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st);
+
+// A batch of slots with identical shapes (uniform per-slot strides).
+struct Batch {
+  Slot* d_slots;
+  std::vector<Slot> h;
+  int n;
+  int max_t, max_td, max_tk, max_m, max_n, max_k;
+  int64_t max_entries, max_pairs;
+  cudaStream_t st;
+  // uniform layout (slot 0 bases and strides, in elements)
+  int np, ndp, kp;
+  int64_t mat_stride, z_stride, s_stride, linv_stride, wd_stride, slinv_stride;
+  // mixed-path workspace
+  bool mixed;
+  int S;
+  uint16_t *PA, *PB, *PBIG;
+  int32_t *EA, *EB, *EBIG;
+  int64_t pa_cap, pb_cap, pbig_cap;   // elements per slot
+  int64_t ea_cap, eb_cap, ebig_cap;   // exponents per slot
+  int32_t* err;
+  int64_t spin_limit;
+};
+
+// mixed blocked routines (eval_mixed.cu)
+int mixed_potrf(Batch& B, int sel);
+int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // W = F^-1 (lower), F by sel
+int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = W^T W (W in L)
+int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S
+int mixed_var_constraint(Batch& B);                           // t2 = diag(Q^-1 C^T S^-1 C Q^-1)
+
+}  // namespace inla

@@ -192,16 +192,17 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
       bstart[b] = s;
       s += D->blocks[b].size;
     }
+    // structured / fixed blocks first, the dense block last: an intercept (or any effect
+    // observed by many rows) is then eliminated first with an exact large pivot, and the
+    // near-null direction it shares with the dense field ends up in pivots of the dense
+    // field's own scale instead of cancelling against the intercept's.
     int p = 0;
-    if (dense_b >= 0) {
-      bstart_int[dense_b] = 0;
-      p = D->blocks[dense_b].size;
-    }
     for (int b = 0; b < D->nblocks; ++b)
       if (b != dense_b) {
         bstart_int[b] = p;
         p += D->blocks[b].size;
       }
+    if (dense_b >= 0) bstart_int[dense_b] = p;
   }
   M->perm.assign(n, 0);
   std::vector<int> block_of_int(n);
@@ -217,6 +218,7 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   d.k_pad = k > 0 ? (int)round_up(k, PAD) : 0;
   d.nd = dense_b >= 0 ? D->blocks[dense_b].size : 0;
   d.nd_pad = d.nd > 0 ? (int)round_up(d.nd, PAD) : 0;
+  d.nd_off = dense_b >= 0 ? bstart_int[dense_b] : 0;
   d.likelihood = D->likelihood;
   d.lik_prec = D->lik_prec;
   d.theta_dim = D->theta_dim;
@@ -394,6 +396,25 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   }
   for (int i = n; i < n_pad; ++i) ent.push_back(PriorEntry{i, i, -1, 0, 1.0, 0.0});
   d.nentries = (int64_t)ent.size();
+  // gamma C^T C (lower triangle, internal indices): added to Q* for the constrained solves.
+  // For x with C x = 0 it changes neither the kriged mode, nor the constrained covariance
+  // N (N^T Q* N)^-1 N^T, nor log|Q*| + log|C Q*^-1 C^T| = log|N^T Q* N| + log|C C^T|
+  // (N an orthonormal basis of null(C)); it lifts the eps-sized eigenvalues of Q* along the
+  // intrinsic null directions to O(gamma), which the reduced-precision factor needs.
+  std::vector<PriorEntry> cct;
+  if (k > 0) {
+    std::map<int64_t, double> acc;
+    for (int r = 0; r < k; ++r)
+      for (int64_t a = D->C_rowptr[r]; a < D->C_rowptr[r + 1]; ++a)
+        for (int64_t b = D->C_rowptr[r]; b < D->C_rowptr[r + 1]; ++b) {
+          const int ia = perm[D->C_col[a]], ib = perm[D->C_col[b]];
+          if (ia < ib) continue;
+          acc[(int64_t)ia * n_pad + ib] += D->C_val[a] * D->C_val[b];
+        }
+    for (auto& kv : acc) cct.push_back(PriorEntry{(int32_t)(kv.first / n_pad), (int32_t)(kv.first % n_pad), -1, 0, kv.second, 0.0});
+  }
+  d.ncct = (int64_t)cct.size();
+  d.gamma_c = 1.0;
   d.prior_const_logdet = const_logdet;
   d.logdet_CCt = 0.0;
   if (k > 0) {
@@ -425,6 +446,7 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   INLA_TRY(dev_copy(M, &d.y, D->y, (size_t)m));
   if (D->offset) INLA_TRY(dev_copy(M, &d.offset, D->offset, (size_t)m));
   INLA_TRY(dev_copy(M, &d.entries, ent.data(), ent.size()));
+  INLA_TRY(dev_copy(M, &d.cct, cct.data(), cct.size()));
   INLA_TRY(dev_copy(M, &d.kron_eig, eig.data(), eig.size()));
   if (dense_b >= 0) {
     const inla_block& B = D->blocks[dense_b];

@@ -1,0 +1,71 @@
+// Ozaki-split GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA).
+//
+// Each operand row is scaled by a power of two per 256-wide K chunk and cut into S slices of
+// 7 bits (integers |v| <= 128 held exactly in BF16):  x = 2^e sum_i v_i 2^{-7(i+1)} + r,
+// |r| <= 2^{e-7S-1}.  A chunk's product is then sum_{i+j<S} 2^{-7(i+j+2)} (V_i W_j^T): every
+// slice product is an integer below 2^14, so the FP32 tensor-core sums over <= 256 terms
+// are exact (< 2^24), and the S groups d = i+j are kept in S separate TMEM accumulators.
+// The epilogue combines them in double-float (FP32 pairs) and updates a double-float C.
+// (Splitting of floating-point operands into error-free slices: Ozaki, Ogita, Oishi, Rump,
+// Numer. Algorithms 59 (2012).)
+#pragma once
+#include <cuda.h>
+#include <cstdint>
+#include "internal.h"
+
+namespace inla {
+
+constexpr int OZ_BM = 128;      // tile rows (tcgen05 M)
+constexpr int OZ_BN = 128;      // tile columns (tcgen05 N)
+constexpr int OZ_BK = 64;       // K per TMA box (128-byte swizzle of BF16)
+constexpr int OZ_CHUNK = 256;   // K per exact accumulation chunk (one exponent per row)
+constexpr int OZ_MAX_S = 4;
+
+// A sliced operand: planes [plane = slot * S + slice][row][k] (BF16, row stride ld_k
+// elements, plane stride plane_stride elements) and exponents [slot][chunk][row] (int32,
+// chunk stride exp_chunk_stride, slot stride exp_slot_stride).
+struct OzOperand {
+  uint16_t* planes;
+  int32_t* exps;
+  int rows;               // valid rows (TMA zero-fills beyond)
+  int K;                  // valid K (multiple of 64)
+  int ld_k;               // row stride in elements (multiple of 64)
+  int64_t plane_stride;   // elements between planes
+  int exp_chunk_stride;   // = rows capacity
+  int64_t exp_slot_stride;
+};
+
+// C (double-float, row-major) = alpha C + beta (A B^T) over [0, M) x [0, N), per slot.
+struct OzArgs {
+  int32_t* expA;
+  int32_t* expB;
+  int expA_chunk_stride, expB_chunk_stride;
+  int64_t expA_slot_stride, expB_slot_stride;
+  float2* C;
+  int64_t C_slot_stride;
+  int ldc;
+  int M, N, K;
+  int k_mode;        // 0: k in [0, K); 1: k >= max(m0, n0); 2: k >= n0; 3: k >= m0
+  int tiles_m, tiles_n;
+  int lower;         // only tiles with tile_m >= tile_n
+  int lower_elems;   // only elements with row >= col
+  float alpha, beta;
+  int S;
+  int64_t spin_limit;
+  int32_t* err;      // device flag: set to nonzero on a timed-out wait
+};
+
+// Host: encode a 3-D tensor map over an operand's planes (box 64 x 128 x 1).
+int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes);
+// Host: C = alpha C + beta A B^T for `nslots` slots (grid.z), S slices.
+int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args, int nslots, cudaStream_t st);
+
+// Slicing kernels (host launchers).  Source element (r, k) of operand row r is
+//   rows:  src[(row0 + r) * ld + col0 + k]      cols: src[(row0 + k) * ld + col0 + r]
+// for r < R, k < K.  `src_slot_stride` in elements.  Source type: df64 (float2) or FP64.
+void oz_slice_df(const float2* src, int64_t src_slot_stride, int ld, int row0, int col0, int R, int K,
+                 bool transposed, const OzOperand& dst, int S, int nslots, cudaStream_t st);
+void oz_slice_f64(const double* src, int64_t src_slot_stride, int ld, int row0, int col0, int R, int K,
+                  bool transposed, const OzOperand& dst, int S, int nslots, cudaStream_t st);
+
+}  // namespace inla

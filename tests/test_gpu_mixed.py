@@ -1,0 +1,103 @@
+"""Mixed-precision path (double-float storage, Ozaki-split tcgen05 GEMMs with S = 4 slices,
+FP64 64 x 64 diagonal tiles) against the FP64 oracle.
+
+Tolerances are the stated targets for the mixed form: |log pi~ - oracle| <= 1e-3 and the
+marginal variances within 1e-4 relative.  The mode is the fixed point of Newton steps whose
+gradient A^T (y - w) - Q_p x is exact up to the error of the mixed-precision prior precision
+Q_p, so x_hat inherits that relative error (~1e-6 observed); it is held to 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import inla_oracle as O
+from paper_2311_08050_gb300 import build as B
+from paper_2311_08050_gb300 import inla, synth
+
+pytestmark = pytest.mark.gpu
+
+LP_ABS = 1e-3
+V_RTOL = 1e-4
+X_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _check(spec, thetas, lp, st, xs, vs, v_rtol=V_RTOL, x_rtol=X_RTOL):
+    errs = []
+    for b, th in enumerate(thetas):
+        r = O.evaluate(spec, th)
+        assert st[b] == 0, inla.status_string(st[b])
+        e_lp = abs(lp[b] - r["log_post"])
+        e_x = np.max(np.abs(xs[b] - r["x_hat"])) / max(1.0, np.max(np.abs(r["x_hat"])))
+        e_v = np.max(np.abs(vs[b] / r["var"] - 1))
+        errs.append((e_lp, e_x, e_v, int(np.argmax(np.abs(vs[b] / r["var"] - 1)))))
+        assert e_lp <= LP_ABS, (b, e_lp)
+        assert e_x <= x_rtol, (b, e_x)
+        assert e_v <= v_rtol, (b, e_v)
+    print("mixed errors (log_post abs, x rel, var rel):", errs)
+    return errs
+
+
+def test_mixed_config1():
+    spec, thetas = synth.config1()
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed", slices=4)
+    _check(spec, thetas, lp, st, xs, vs)
+
+
+def test_precision_ladder_error_decreases_with_slices():
+    """Each extra 7-bit slice should cut the log pi~ error against the oracle (2^-7 per rung
+    in the truncation term); the error must fall monotonically from 2 to 4 slices."""
+    spec, thetas = synth.config1()
+    m = inla.Model(spec)
+    r = O.evaluate(spec, thetas[0])
+    errs = []
+    for S in (2, 3, 4):
+        lp, st, _, _ = inla.eval_batch([m], thetas[:1], precision="mixed", slices=S, want_x=False, want_var=False)
+        assert st[0] == 0
+        errs.append(abs(lp[0] - r["log_post"]))
+    print("ladder errors", errs)
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_mixed_ragged_with_offset():
+    spec = synth.spatial_poisson("ragged", 7, 299, 900, [0.1, np.log(0.15)])
+    spec.offset = np.random.default_rng(1).normal(0.2, 0.3, spec.m)
+    thetas = np.array([[0.1, np.log(0.15)], [-0.3, np.log(0.3)]])
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
+    _check(spec, thetas, lp, st, xs, vs)
+
+
+def test_mixed_constrained_spacetime():
+    spec = synth.spacetime_age("small_st", 11, n_s=8, n_t=6, n_a=4)
+    thetas = np.array([[1.0, 2.0, 3.0, 4.0, 1.0, 2.0], [0.5, 1.5, 2.5, 3.0, 0.0, 1.0]])
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
+    _check(spec, thetas, lp, st, xs, vs)
+    C = spec.C.to_dense()
+    for x in xs:
+        # the kriging correction runs in the mixed precision: C x_hat = 0 to ~1e-7
+        assert np.max(np.abs(C @ x)) < 1e-6
+
+
+def test_mixed_gaussian_uneven_groups():
+    specs = [synth.gaussian_spatial(f"g{n}", 100 + n, n) for n in (100, 333)]
+    ms = [inla.Model(s) for s in specs]
+    thetas = np.array([[0.0, np.log(0.2)], [0.2, np.log(0.1)], [-0.1, np.log(0.3)]])
+    which = np.array([1, 0, 1], dtype=np.int32)
+    lp, st, xs, vs = inla.eval_batch(ms, thetas, model_of_theta=which, precision="mixed")
+    for b in range(3):
+        _check(specs[which[b]], thetas[b:b + 1], lp[b:b + 1], st[b:b + 1], xs[b:b + 1], vs[b:b + 1])
+
+
+@pytest.mark.slow
+def test_mixed_config2_subset():
+    spec, thetas = synth.config2()
+    sub = thetas[[0, 5]]
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], sub, precision="mixed")
+    _check(spec, sub, lp, st, xs, vs)
