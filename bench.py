@@ -101,9 +101,14 @@ def _dist_env():
     return rank, world, local
 
 
-def _workload(rank):
+WORKLOADS = {5: "poisson_n16384_m100000_fd9", 2: "poisson_n4096_m20000_fd7", 1: "poisson_n256_m1000_5pts"}
+
+
+def _workload(rank, config=5):
+    """The n = 16384 workload is the benchmark; the smaller configurations exist only for
+    profiling captures (a few GB on the device)."""
     from paper_2311_08050_gb300 import synth
-    spec, thetas = synth.config5()
+    spec, thetas = synth.CONFIGS[config]()
     if rank:  # weak scaling: every rank evaluates its own FD batch (shifted centre)
         thetas = thetas + 0.01 * rank
     return spec, thetas
@@ -123,7 +128,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import inla_oracle as O
-    spec, thetas = _workload(0)
+    spec, thetas = _workload(0, args.config)
     times = []
     t_start = time.time()
     k = 0
@@ -139,7 +144,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": spec.n, "m": spec.m, "batch": len(thetas),
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.config], "n": spec.n, "m": spec.m, "batch": len(thetas),
                                             "parallelism": "host cores (numpy/scipy LAPACK)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "full oracle evaluation of one FD theta point per step (n=16384)"},
@@ -160,7 +165,7 @@ def run_ours(args):
     L = inla.lib()
     L.inla_test_stats_read.argtypes = [C.POINTER(C.c_double)]
     L.inla_test_launch_count.restype = C.c_int64
-    spec, thetas = _workload(rank)
+    spec, thetas = _workload(rank, args.config)
     nb = len(thetas)
     model = inla.Model(spec)
     stream = torch.cuda.Stream()
@@ -170,7 +175,8 @@ def run_ours(args):
     vbuf = torch.empty((nb, n), dtype=torch.float64, device="cuda")
     xp = [xbuf[b].data_ptr() for b in range(nb)]
     vp = [vbuf[b].data_ptr() for b in range(nb)]
-    kw = dict(precision=args.precision, slices=args.slices, stream=sptr, device_out=True, x_out=xp, var_out=vp)
+    kw = dict(precision=args.precision, slices=args.slices, newton_slices=args.newton_slices, stream=sptr,
+              device_out=True, x_out=xp, var_out=vp)
 
     def step():
         lp, st, _, _ = inla.eval_batch([model], thetas, **kw)
@@ -208,33 +214,46 @@ def run_ours(args):
     value = world * nb * args.steps / t_max
     # ---------------- roofline of the dominant kernel (instrumented extra step) ----------------
     L.inla_test_stats_enable(1)
+    L.inla_test_profile_enable(1)
     step()
     torch.cuda.synchronize()
     L.inla_test_stats_enable(0)
+    L.inla_test_profile_enable(0)
     stats = (C.c_double * 4)()
     L.inla_test_stats_read(stats)
+    pbuf = C.create_string_buffer(1 << 16)
+    L.inla_test_profile_read(pbuf, 1 << 16)
+    breakdown = []
+    for line in pbuf.value.decode().splitlines():
+        name, cnt, tot = line.split()
+        breakdown.append({"kernel": name, "launches": int(cnt), "ms": round(float(tot), 3)})
+    step_ms_prof = sum(b["ms"] for b in breakdown) or 1.0
+    for b in breakdown:
+        b["share"] = round(b["ms"] / step_ms_prof, 4)
     launches, alg, tens, kms = stats[0], stats[1], stats[2], stats[3]
     peaks, psrc = _peaks()
     peak_tc = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     tens_rate = tens / (kms / 1e3) / 1e12 if kms > 0 else None
     alg_rate = alg / (kms / 1e3) / 1e12 if kms > 0 else None
-    roofline = {"bound": "tensor", "kernel": f"k_ozaki_gemm<{args.slices}> (tcgen05 BF16 slices)",
+    roofline = {"bound": "tensor", "kernel": "k_ozaki_gemm<S> (tcgen05 BF16 slices)",
                 "achieved": tens_rate, "peak": peak_tc, "unit": "TFLOP/s",
                 "frac": (tens_rate / peak_tc) if tens_rate else None, "traffic": None,
-                "algorithmic_tflops": alg_rate, "passes_per_flop": args.slices * (args.slices + 1) // 2,
+                "algorithmic_tflops": alg_rate, "passes_per_flop": round(tens / alg, 2) if alg else None,
                 "launches_per_step": int(launches), "kernel_ms_per_step": kms,
                 "peak_source": f"{psrc} bf16 sustained (kernel timed inside a long step)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": f"bf16x{args.slices} slices (exact fp32 accumulation) + df64 storage + f64 diagonal tiles"
+           "dtype": f"bf16 Ozaki slices x{args.slices} (prior, final factor) / x{args.newton_slices} (Newton), "
+                    "exact fp32 accumulation + df64 storage + f64 diagonal tiles"
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
-           "config": {"workload": WORKLOAD, "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
+           "config": {"workload": WORKLOADS[args.config], "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
                       "precision": args.precision, "slices": args.slices,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
-           "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None}
+           "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
+           "kernel_breakdown": breakdown[:12]}
     # ---------------- end to end from host buffers ----------------
     if not args.no_e2e:
         from paper_2311_08050_gb300.synth import ModelSpec  # noqa: F401
@@ -242,7 +261,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             m2 = inla.Model(spec)
-            lp2, st2, xs2, vs2 = inla.eval_batch([m2], thetas, precision=args.precision, slices=args.slices)
+            lp2, st2, xs2, vs2 = inla.eval_batch([m2], thetas, precision=args.precision, slices=args.slices,
+                                                 newton_slices=args.newton_slices)
             m2.close()
         t_e2e = time.perf_counter() - t0
         out["e2e"] = {"value": nb * e2e_steps / t_e2e * world, "unit": UNIT,
@@ -251,8 +271,10 @@ def run_ours(args):
     # ---------------- FP64 GPU path on one theta (comparison) ----------------
     if not args.no_fp64 and args.precision == "mixed":
         t0 = time.perf_counter()
+        x64 = torch.empty((1, n), dtype=torch.float64, device="cuda")
+        v64 = torch.empty((1, n), dtype=torch.float64, device="cuda")
         lp64, st64, _, _ = inla.eval_batch([model], thetas[:1], precision="fp64", stream=sptr, device_out=True,
-                                           x_out=xp[:1], var_out=vp[:1])
+                                           x_out=[x64[0].data_ptr()], var_out=[v64[0].data_ptr()])
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         out["fp64"] = {"value": 1.0 / t64, "unit": UNIT, "thetas_timed": 1, "seconds": t64,
@@ -288,11 +310,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--slices", type=int, default=5, help="slices of the prior inversion and the factor at the mode")
+    ap.add_argument("--newton-slices", type=int, default=4, help="slices of the Newton-step factorisations")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=150.0)
+    ap.add_argument("--config", type=int, default=5, choices=[5, 2, 1],
+                    help="5: the benchmark workload; 2 / 1: smaller cases for profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

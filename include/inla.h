@@ -107,7 +107,10 @@ typedef struct {
 
 typedef struct {
   int32_t precision;   /* INLA_FP64 or INLA_MIXED */
-  int32_t slices;      /* INLA_MIXED: BF16 slices per operand (2..4); 0 = default */
+  int32_t slices;      /* INLA_MIXED: BF16 slices per operand (2..5) for the prior inversion and
+                          the factor at the mode (log-det, variances); 0 = default (5) */
+  int32_t newton_slices; /* INLA_MIXED: slices for the Newton-step factorisations, which only
+                          steer convergence (the gradient is exact); 0 = min(4, slices) */
   double newton_tol;   /* infinity-norm step tolerance (default 1e-8) */
   int32_t newton_max;  /* maximum Newton iterations (default 50) */
   int64_t spin_limit;  /* iteration limit of every device-side wait (default 1<<26) */

@@ -40,6 +40,12 @@ int inla_test_stats_read(double *out);
 /* Number of CUDA kernels the library launched since the previous call (then reset). */
 int64_t inla_test_launch_count(void);
 
+/* Per-kernel profile: while enabled, a CUDA event is recorded on the evaluation stream
+ * before every launch.  inla_test_profile_read writes "name launches total_ms" lines
+ * (largest total first) into buf and resets; it returns the bytes written. */
+void inla_test_profile_enable(int on);
+int inla_test_profile_read(char *buf, int len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -247,6 +247,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   }
   sync_active(B);
   // ---------------- prior precision ----------------
+  B.S = B.S_exact;
   launch_theta_prior(B.d_slots, NB, B.st);
   for (int i = 0; i < NB; ++i) cudaMemsetAsync(B.h[i].Qp, 0, (size_t)B.h[i].n_pad * B.h[i].n_pad * 8, B.st);
   INLA_TRY(debug_check(B.st, "prior start"));
@@ -261,6 +262,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
     if (info[2 * i] & INFO_NOT_SPD) fail_slot(B, status, i, INLA_E_NOT_SPD);
   sync_active(B);
   // ---------------- Newton iterations ----------------
+  B.S = B.S_newton;
   launch_zero_vec(B.d_slots, NB, 0, B.max_n, B.st);
   launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
   op_qp_gemv(B, 0);
@@ -272,23 +274,29 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   INLA_CUDA_TRY(cudaMallocAsync((void**)&d_flags, sizeof(int) * NB, B.st));
   std::vector<int> flags(NB, 0);
   int rc = INLA_OK;
+  double last_step = 1e300;
+  bool reuse_ok = true;
   for (int it = 1; it <= o.newton_max && rc == INLA_OK; ++it) {
     int nact = 0;
     for (int i = 0; i < NB; ++i) nact += B.h[i].active;
     if (nact == 0) break;
     for (int i = 0; i < NB; ++i)
       if (B.h[i].active) iters[i] = it;
-    // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction
-    op_assemble_q(B);
+    // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction.  The mixed path reuses
+    // the last factor once the steps are small and shrinking fast (modified Newton): the
+    // gradient stays exact, so the fixed point is unchanged; a reused step that does not
+    // shrink the step by 4x forces a fresh factor at the next iteration.
+    const bool refactor = !B.mixed || it <= 2 || last_step > 1e-2 || !reuse_ok;
+    if (refactor) op_assemble_q(B);
     launch_gradient(B.d_slots, NB, B.max_n, B.st);
     if ((rc = debug_check(B.st, "newton assemble")) != INLA_OK) break;
-    if ((rc = op_potrf(B, SEL_L)) != INLA_OK) break;
+    if (refactor && (rc = op_potrf(B, SEL_L)) != INLA_OK) break;
     if ((rc = debug_check(B.st, "newton potrf")) != INLA_OK) break;
     solve_llt(B, SEL_L, V_G, V_T2, V_G);
     if ((rc = debug_check(B.st, "newton solve")) != INLA_OK) break;
     launch_newton_xu(B.d_slots, NB, B.max_n, B.st);
     if (B.max_k > 0) {
-      if ((rc = op_schur(B)) != INLA_OK) break;
+      if (refactor && (rc = op_schur(B)) != INLA_OK) break;
       launch_cx(B.d_slots, NB, B.max_k, B.st);
       solve_llt(B, SEL_S, V_KV1, V_KV2, V_KV1);
       if (B.mixed) launch_z_gemv_df(B.d_slots, NB, B.max_n, B.st);
@@ -322,6 +330,13 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
     }
     if (rc != INLA_OK) break;
     launch_accept(B.d_slots, NB, B.max_n, B.st);
+    {
+      double mx = 0.0;
+      for (int i = 0; i < NB; ++i)
+        if (B.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
+      reuse_ok = refactor || mx < 0.25 * last_step;
+      last_step = mx;
+    }
     for (int i = 0; i < NB; ++i) {
       if (!B.h[i].active) continue;
       const double* oi = &out[(size_t)i * SLOT_NOUT];
@@ -345,6 +360,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   }
   sync_active(B);
   // ---------------- at the mode ----------------
+  B.S = B.S_exact;
   launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
   op_qp_gemv(B, 0);
   op_assemble_q(B);
@@ -516,9 +532,12 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   if (o.spin_limit <= 0) o.spin_limit = (int64_t)1 << 26;
   if (o.precision != INLA_FP64 && o.precision != INLA_MIXED) return INLA_E_BADARG;
   const bool mixed = o.precision == INLA_MIXED;
-  const int S = mixed ? (o.slices == 0 ? 4 : o.slices) : 0;
-  if (mixed && (S < 2 || S > OZ_MAX_S)) return INLA_E_BADARG;
+  const int S_exact = mixed ? (o.slices == 0 ? 5 : o.slices) : 0;
+  const int S_newton = mixed ? (o.newton_slices == 0 ? std::min(4, S_exact) : o.newton_slices) : 0;
+  if (mixed && (S_exact < 2 || S_exact > OZ_MAX_S || S_newton < 2 || S_newton > OZ_MAX_S)) return INLA_E_BADARG;
+  const int S = std::max(S_exact, S_newton);  // workspace capacity
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+  prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
   const bool want_var = var != nullptr;
   int theta_dim = -1;
@@ -589,6 +608,8 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     Bt.n = G;
     Bt.st = st;
     Bt.spin_limit = o.spin_limit;
+    Bt.S_exact = S_exact;
+    Bt.S_newton = S_newton;
     Bt.max_t = d0.n_pad / TB;
     Bt.max_td = d0.nd_pad / TB;
     Bt.max_tk = d0.k_pad / TB;
@@ -657,7 +678,7 @@ __global__ void k_gather(double* dst, const double* src, const int32_t* perm, in
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[perm[i]];
 }
 void launch_gather(double* dst, const double* src, const int32_t* perm, int n, cudaStream_t st) {
-  count_launch(), k_gather<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(dst, src, perm, n);
+  count_launch("k_gather"), k_gather<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(dst, src, perm, n);
 }
 
 }  // namespace inla

@@ -209,7 +209,7 @@ __global__ void k_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n)
     W[(int64_t)i * ld + i] = make_float2(1.f, 0.f);
 }
 void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st) {
-  count_launch(), k_diag_ones_df<<<dim3(std::min(1024, (n + 255) / 256), nslots), 256, 0, st>>>(base, slot_stride, ld, n);
+  count_launch("k_diag_ones_df"), k_diag_ones_df<<<dim3(std::min(1024, (n + 255) / 256), nslots), 256, 0, st>>>(base, slot_stride, ld, n);
 }
 
 }  // namespace inla

@@ -146,8 +146,8 @@ bool debug_sync_enabled();
 int debug_check(cudaStream_t st, const char* site);
 // number of kernels this library has launched (read and reset by inla_test_launch_count)
 extern int64_t g_kernel_launches;
-inline int count_launch() {
-  ++g_kernel_launches;
-  return 0;
-}
+// called before every kernel launch: counts it and, while the profiler is on, records a CUDA
+// event on the profiled stream so that per-kernel times can be attributed (prof.cu)
+int count_launch(const char* name);
+void prof_set_stream(cudaStream_t st);
 }  // namespace inla

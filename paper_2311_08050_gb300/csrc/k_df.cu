@@ -181,17 +181,20 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int
       a[j][j] = sqrt(d);
     }
     __syncthreads();
-    const double djj = a[j][j];
-    for (int i = j + 1 + tid; i < TB; i += blockDim.x) a[i][j] = a[i][j] / djj;
+    const double rdjj = 1.0 / a[j][j];
+    for (int i = j + 1 + tid; i < TB; i += blockDim.x) a[i][j] = a[i][j] * rdjj;
     __syncthreads();
     for (int i = j + 1 + ty; i < TB; i += 16)
       for (int c = j + 1 + tx; c <= i; c += 16) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
     __syncthreads();
   }
+  __shared__ double rdiag[TB];
+  if (tid < TB) rdiag[tid] = 1.0 / a[tid][tid];
+  __syncthreads();
   if (tid < TB) {
     const int c = tid;
     for (int i = 0; i < c; ++i) inv[i][c] = 0.0;
-    inv[c][c] = 1.0 / a[c][c];
+    inv[c][c] = rdiag[c];
     for (int i = c + 1; i < TB; ++i) {
       double acc0 = 0.0, acc1 = 0.0;
       int k = c;
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int
         acc1 = fma(a[i][k + 1], inv[k + 1][c], acc1);
       }
       if (k < i) acc0 = fma(a[i][k], inv[k][c], acc0);
-      inv[i][c] = -(acc0 + acc1) / a[i][i];
+      inv[i][c] = -(acc0 + acc1) * rdiag[i];
     }
   }
   __syncthreads();
@@ -348,31 +351,31 @@ static int tri(int t) { return t * (t + 1) / 2; }
 static int vgrid(int n) { return std::min(1024, std::max(1, (n + 255) / 256)); }
 
 void launch_cov_to_df(Slot* slots, int nslots, int max_td, cudaStream_t st) {
-  if (max_td > 0) count_launch(), k_cov_to_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
+  if (max_td > 0) count_launch("k_cov_to_df"), k_cov_to_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
 }
 void launch_prior_entries_df(Slot* slots, int nslots, int64_t max_entries, cudaStream_t st) {
   if (max_entries > 0)
-    count_launch(), k_prior_entries_df<<<dim3((unsigned)std::min<int64_t>(2048, (max_entries + 255) / 256), nslots), 256, 0, st>>>(slots);
+    count_launch("k_prior_entries_df"), k_prior_entries_df<<<dim3((unsigned)std::min<int64_t>(2048, (max_entries + 255) / 256), nslots), 256, 0, st>>>(slots);
 }
 void launch_add_pairs_df(Slot* slots, int nslots, int64_t max_pairs, cudaStream_t st) {
   if (max_pairs > 0)
-    count_launch(), k_add_pairs_df<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
+    count_launch("k_add_pairs_df"), k_add_pairs_df<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_qp_gemv_df(Slot* slots, int nslots, int which, int max_n, cudaStream_t st) {
-  count_launch(), k_vec_to_df<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
-  count_launch(), k_qp_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots, which);
+  count_launch("k_vec_to_df"), k_vec_to_df<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
+  count_launch("k_qp_gemv_df"), k_qp_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots, which);
 }
 void launch_z_gemv_df(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_z_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
+  count_launch("k_z_gemv_df"), k_z_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st) {
-  count_launch(), k_ct_fill_df<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
+  count_launch("k_ct_fill_df"), k_ct_fill_df<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
 void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st) {
-  count_launch(), k_s_pad_identity<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
+  count_launch("k_s_pad_identity"), k_s_pad_identity<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
 void launch_set_identity_df(Slot* slots, int nslots, int which_wk, int size_sel, int max_t, cudaStream_t st) {
-  count_launch(), k_set_identity_df<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots, which_wk, size_sel);
+  count_launch("k_set_identity_df"), k_set_identity_df<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots, which_wk, size_sel);
 }
 void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st) {
   static bool init = false;
@@ -381,22 +384,22 @@ void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t
     cudaFuncSetAttribute(k_potrf_diag_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     init = true;
   }
-  count_launch(), k_potrf_diag_df<<<nslots, 256, smem, st>>>(slots, sel, kt);
+  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, smem, st>>>(slots, sel, kt);
 }
 void launch_trsv_fwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t, cudaStream_t st) {
-  count_launch(), k_trsv_fwd_df<<<dim3(max_t - kt, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
+  count_launch("k_trsv_fwd_df"), k_trsv_fwd_df<<<dim3(max_t - kt, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
 }
 void launch_trsv_bwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, cudaStream_t st) {
-  count_launch(), k_trsv_bwd_df<<<dim3(kt + 1, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
+  count_launch("k_trsv_bwd_df"), k_trsv_bwd_df<<<dim3(kt + 1, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
 }
 void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st) {
-  count_launch(), k_logdet_df<<<nslots, 256, 0, st>>>(slots, sel, out_idx);
+  count_launch("k_logdet_df"), k_logdet_df<<<nslots, 256, 0, st>>>(slots, sel, out_idx);
 }
 void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st) {
-  count_launch(), k_colsumsq_wk_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
+  count_launch("k_colsumsq_wk_df"), k_colsumsq_wk_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
 }
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st) {
-  count_launch(), k_colsumsq_gt_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
+  count_launch("k_colsumsq_gt_df"), k_colsumsq_gt_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
 }
 
 }  // namespace inla
@@ -413,6 +416,6 @@ __global__ void k_add_cct_df(Slot* slots) {
   }
 }
 void launch_add_cct_df(Slot* slots, int nslots, cudaStream_t st) {
-  count_launch(), k_add_cct_df<<<dim3(1024, nslots), 256, 0, st>>>(slots);
+  count_launch("k_add_cct_df"), k_add_cct_df<<<dim3(1024, nslots), 256, 0, st>>>(slots);
 }
 }  // namespace inla

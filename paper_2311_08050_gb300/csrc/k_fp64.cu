@@ -474,60 +474,60 @@ void launch_potrf_diag(Slot* slots, int nslots, int sel, int kt, int max_t, cuda
     cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     init = true;
   }
-  count_launch(), k_potrf_diag<<<nslots, 256, smem, st>>>(slots, sel, kt);
+  count_launch("k_potrf_diag"), k_potrf_diag<<<nslots, 256, smem, st>>>(slots, sel, kt);
 }
 void launch_trsm_panel(Slot* slots, int nslots, int sel, int kt, int max_t, cudaStream_t st) {
   if (max_t - kt - 1 <= 0) return;
-  count_launch(), k_trsm_panel<<<dim3(max_t - kt - 1, nslots), 256, 0, st>>>(slots, sel, kt);
+  count_launch("k_trsm_panel"), k_trsm_panel<<<dim3(max_t - kt - 1, nslots), 256, 0, st>>>(slots, sel, kt);
 }
 void launch_syrk_update(Slot* slots, int nslots, int sel, int kt, int max_t, cudaStream_t st) {
   const int t = max_t - kt - 1;
   if (t <= 0) return;
-  count_launch(), k_syrk_update<<<dim3(tri(t), nslots), 256, 0, st>>>(slots, sel, kt);
+  count_launch("k_syrk_update"), k_syrk_update<<<dim3(tri(t), nslots), 256, 0, st>>>(slots, sel, kt);
 }
 void launch_trtri_step(Slot* slots, int nslots, int sel, int dst, int jt, int max_t, cudaStream_t st) {
-  if (max_t - jt - 1 > 0) count_launch(), k_trtri_gemm<<<dim3(max_t - jt - 1, nslots), 256, 0, st>>>(slots, sel, dst, jt);
-  count_launch(), k_trtri_scale<<<dim3(max_t - jt, nslots), 256, 0, st>>>(slots, sel, dst, jt);
+  if (max_t - jt - 1 > 0) count_launch("k_trtri_gemm"), k_trtri_gemm<<<dim3(max_t - jt - 1, nslots), 256, 0, st>>>(slots, sel, dst, jt);
+  count_launch("k_trtri_scale"), k_trtri_scale<<<dim3(max_t - jt, nslots), 256, 0, st>>>(slots, sel, dst, jt);
 }
 void launch_lauum_cov(Slot* slots, int nslots, int max_td, cudaStream_t st) {
   if (max_td <= 0) return;
-  count_launch(), k_lauum_cov<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
+  count_launch("k_lauum_cov"), k_lauum_cov<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
 }
 void launch_fwd_rhs_step(Slot* slots, int nslots, int kt, int max_t, int max_tk, cudaStream_t st) {
-  count_launch(), k_fwd_rhs_diag<<<dim3(max_tk, nslots), 256, 0, st>>>(slots, kt);
+  count_launch("k_fwd_rhs_diag"), k_fwd_rhs_diag<<<dim3(max_tk, nslots), 256, 0, st>>>(slots, kt);
   if (max_t - kt - 1 > 0)
-    count_launch(), k_fwd_rhs_upd<<<dim3((max_t - kt - 1) * max_tk, nslots), 256, 0, st>>>(slots, kt, max_tk);
+    count_launch("k_fwd_rhs_upd"), k_fwd_rhs_upd<<<dim3((max_t - kt - 1) * max_tk, nslots), 256, 0, st>>>(slots, kt, max_tk);
 }
 void launch_schur_syrk(Slot* slots, int nslots, int max_tk, int max_t, cudaStream_t st) {
   (void)max_t;
-  count_launch(), k_schur_syrk<<<dim3(tri(max_tk), nslots), 256, 0, st>>>(slots);
+  count_launch("k_schur_syrk"), k_schur_syrk<<<dim3(tri(max_tk), nslots), 256, 0, st>>>(slots);
 }
 void launch_zt_w(Slot* slots, int nslots, int max_tk, int max_t, cudaStream_t st) {
-  count_launch(), k_zt_w<<<dim3(max_tk * max_t, nslots), 256, 0, st>>>(slots, max_t);
+  count_launch("k_zt_w"), k_zt_w<<<dim3(max_tk * max_t, nslots), 256, 0, st>>>(slots, max_t);
 }
 void launch_fwd_s_rhs_step(Slot* slots, int nslots, int kt, int max_tk, int max_t, cudaStream_t st) {
-  count_launch(), k_fwd_s_diag<<<dim3(max_t, nslots), 256, 0, st>>>(slots, kt);
+  count_launch("k_fwd_s_diag"), k_fwd_s_diag<<<dim3(max_t, nslots), 256, 0, st>>>(slots, kt);
   if (max_tk - kt - 1 > 0)
-    count_launch(), k_fwd_s_upd<<<dim3((max_tk - kt - 1) * max_t, nslots), 256, 0, st>>>(slots, kt, max_t);
+    count_launch("k_fwd_s_upd"), k_fwd_s_upd<<<dim3((max_tk - kt - 1) * max_t, nslots), 256, 0, st>>>(slots, kt, max_t);
 }
 void launch_trsv_fwd_step(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t,
                           cudaStream_t st) {
-  count_launch(), k_trsv_fwd<<<dim3(max_t - kt, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
+  count_launch("k_trsv_fwd"), k_trsv_fwd<<<dim3(max_t - kt, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
 }
 void launch_trsv_bwd_step(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t,
                           cudaStream_t st) {
   (void)max_t;
-  count_launch(), k_trsv_bwd<<<dim3(kt + 1, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
+  count_launch("k_trsv_bwd"), k_trsv_bwd<<<dim3(kt + 1, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
 }
 void launch_colsumsq_wk(Slot* slots, int nslots, int max_t, cudaStream_t st) {
-  count_launch(), k_colsumsq_wk<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
+  count_launch("k_colsumsq_wk"), k_colsumsq_wk<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
 }
 void launch_colsumsq_gt(Slot* slots, int nslots, int max_tk, int max_t, cudaStream_t st) {
   (void)max_tk;
-  count_launch(), k_colsumsq_gt<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
+  count_launch("k_colsumsq_gt"), k_colsumsq_gt<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
 }
 void launch_logdet(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st) {
-  count_launch(), k_logdet<<<nslots, 256, 0, st>>>(slots, sel, out_idx);
+  count_launch("k_logdet"), k_logdet<<<nslots, 256, 0, st>>>(slots, sel, out_idx);
 }
 
 }  // namespace inla

@@ -245,15 +245,18 @@ __global__ void __launch_bounds__(256) k_quad(Slot* slots, int which) {
   if (threadIdx.x == 0) s.out[OUT_QUAD] = a;
 }
 
-// g = A^T r - t1
+// g = A^T r - t1, one warp per latent entry (a column of A such as an intercept can carry
+// every observation); lanes stride the column, fixed-order shuffle reduction
 __global__ void __launch_bounds__(256) k_gradient(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
   const ModelDev& md = *s.md;
-  for (int j = blockIdx.x * 256 + threadIdx.x; j < s.n_pad; j += gridDim.x * 256) {
+  const int lane = threadIdx.x & 31;
+  for (int j = (blockIdx.x * 256 + threadIdx.x) >> 5; j < s.n_pad; j += (gridDim.x * 256) >> 5) {
     double a = 0.0;
-    for (int64_t e = md.At_rowptr[j]; e < md.At_rowptr[j + 1]; ++e) a = fma(md.At_val[e], s.eta[md.At_row[e]], a);
-    s.g[j] = a - s.t1[j];
+    for (int64_t e = md.At_rowptr[j] + lane; e < md.At_rowptr[j + 1]; e += 32) a = fma(md.At_val[e], s.eta[md.At_row[e]], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) s.g[j] = a - s.t1[j];
   }
 }
 
@@ -366,67 +369,67 @@ static int tri(int t) { return t * (t + 1) / 2; }
 static int vgrid(int n) { return min(1024, max(1, (n + 255) / 256)); }
 
 void launch_cov_build(Slot* slots, int nslots, int max_td, cudaStream_t st) {
-  if (max_td > 0) count_launch(), k_cov_build<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
+  if (max_td > 0) count_launch("k_cov_build"), k_cov_build<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
 }
 void launch_prior_entries(Slot* slots, int nslots, int64_t max_entries, cudaStream_t st) {
-  if (max_entries > 0) count_launch(), k_prior_entries<<<dim3((unsigned)std::min<int64_t>(2048, (max_entries + 255) / 256), nslots), 256, 0, st>>>(slots);
+  if (max_entries > 0) count_launch("k_prior_entries"), k_prior_entries<<<dim3((unsigned)std::min<int64_t>(2048, (max_entries + 255) / 256), nslots), 256, 0, st>>>(slots);
 }
 void launch_mirror_qp(Slot* slots, int nslots, int max_t, cudaStream_t st) {
-  count_launch(), k_mirror_qp<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots);
+  count_launch("k_mirror_qp"), k_mirror_qp<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots);
 }
 void launch_copy_qp_to_l(Slot* slots, int nslots, int max_t, cudaStream_t st) {
-  count_launch(), k_copy_qp_to_l<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots);
+  count_launch("k_copy_qp_to_l"), k_copy_qp_to_l<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots);
 }
 void launch_add_pairs(Slot* slots, int nslots, int64_t max_pairs, cudaStream_t st) {
-  if (max_pairs > 0) count_launch(), k_add_pairs<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
+  if (max_pairs > 0) count_launch("k_add_pairs"), k_add_pairs<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
-void launch_prior_logdet(Slot* slots, int nslots, cudaStream_t st) { count_launch(), k_prior_logdet<<<nslots, 256, 0, st>>>(slots); }
-void launch_theta_prior(Slot* slots, int nslots, cudaStream_t st) { count_launch(), k_theta_prior<<<nslots, 32, 0, st>>>(slots); }
+void launch_prior_logdet(Slot* slots, int nslots, cudaStream_t st) { count_launch("k_prior_logdet"), k_prior_logdet<<<nslots, 256, 0, st>>>(slots); }
+void launch_theta_prior(Slot* slots, int nslots, cudaStream_t st) { count_launch("k_theta_prior"), k_theta_prior<<<nslots, 32, 0, st>>>(slots); }
 void launch_eval_lik(Slot* slots, int nslots, int which, int max_m, cudaStream_t st) {
   (void)max_m;
-  count_launch(), k_eval_lik<<<dim3(128, nslots), 256, 0, st>>>(slots, which);
-  count_launch(), k_finish_sum<<<nslots, 32, 0, st>>>(slots, 128, OUT_LOGLIK);
+  count_launch("k_eval_lik"), k_eval_lik<<<dim3(128, nslots), 256, 0, st>>>(slots, which);
+  count_launch("k_finish_sum"), k_finish_sum<<<nslots, 32, 0, st>>>(slots, 128, OUT_LOGLIK);
 }
 void launch_qp_gemv(Slot* slots, int nslots, int which, int max_n, cudaStream_t st) {
-  count_launch(), k_qp_gemv<<<dim3(min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots, which);
-  count_launch(), k_quad<<<nslots, 256, 0, st>>>(slots, which);
+  count_launch("k_qp_gemv"), k_qp_gemv<<<dim3(min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots, which);
+  count_launch("k_quad"), k_quad<<<nslots, 256, 0, st>>>(slots, which);
 }
-void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st) { count_launch(), k_quad<<<nslots, 256, 0, st>>>(slots, which); }
+void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st) { count_launch("k_quad"), k_quad<<<nslots, 256, 0, st>>>(slots, which); }
 void launch_gradient(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_gradient<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
+  count_launch("k_gradient"), k_gradient<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_newton_xu(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_newton_xu<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
+  count_launch("k_newton_xu"), k_newton_xu<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
 }
 void launch_cx(Slot* slots, int nslots, int max_k, cudaStream_t st) {
-  count_launch(), k_cx<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
+  count_launch("k_cx"), k_cx<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
 void launch_z_gemv(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_z_gemv<<<dim3(min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
+  count_launch("k_z_gemv"), k_z_gemv<<<dim3(min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_krige_apply(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_krige_apply<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
+  count_launch("k_krige_apply"), k_krige_apply<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
 }
 void launch_step_norm(Slot* slots, int nslots, int max_n, cudaStream_t st) {
   (void)max_n;
-  count_launch(), k_step_norm<<<nslots, 256, 0, st>>>(slots);
+  count_launch("k_step_norm"), k_step_norm<<<nslots, 256, 0, st>>>(slots);
 }
 void launch_halve(Slot* slots, int nslots, const int* flags, int max_n, cudaStream_t st) {
-  count_launch(), k_halve<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, flags);
+  count_launch("k_halve"), k_halve<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, flags);
 }
 void launch_accept(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_accept<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
+  count_launch("k_accept"), k_accept<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
 }
 void launch_zero_vec(Slot* slots, int nslots, int which, int max_n, cudaStream_t st) {
-  count_launch(), k_zero_vec<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
+  count_launch("k_zero_vec"), k_zero_vec<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
 }
 void launch_ct_fill(Slot* slots, int nslots, int max_k, cudaStream_t st) {
-  count_launch(), k_ct_fill<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
+  count_launch("k_ct_fill"), k_ct_fill<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
 void launch_var_finish(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch(), k_var_finish<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
+  count_launch("k_var_finish"), k_var_finish<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);
 }
-void launch_assemble(Slot* slots, int nslots, cudaStream_t st) { count_launch(), k_assemble<<<nslots, 32, 0, st>>>(slots); }
+void launch_assemble(Slot* slots, int nslots, cudaStream_t st) { count_launch("k_assemble"), k_assemble<<<nslots, 32, 0, st>>>(slots); }
 
 }  // namespace inla
 
@@ -442,6 +445,6 @@ __global__ void k_add_cct(Slot* slots) {
   }
 }
 void launch_add_cct(Slot* slots, int nslots, cudaStream_t st) {
-  count_launch(), k_add_cct<<<dim3(1024, nslots), 256, 0, st>>>(slots);
+  count_launch("k_add_cct"), k_add_cct<<<dim3(1024, nslots), 256, 0, st>>>(slots);
 }
 }  // namespace inla

@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(320, 1)
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  constexpr uint32_t TMEM_COLS = S * OZ_BN <= 256 ? 256 : 512;
+  // slice-order groups d = i + j >= NACC-1 share the last accumulator (see ozaki.h)
+  constexpr int NACC = S < OZ_NACC ? S : OZ_NACC;
+  constexpr uint32_t TMEM_COLS = NACC * OZ_BN <= 256 ? 256 : 512;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                  "n"(TMEM_COLS));
@@ -211,10 +213,12 @@ __global__ void __launch_bounds__(320, 1)
           const uint32_t a_addr = smem_u32(Abuf + sa * A_BYTES);
           for (int j = 0; j < S - i; ++j) {
             const uint32_t b_addr = smem_u32(Bbuf + (b * S + j) * B_BYTES);
-            const uint32_t d_tmem = tmem + (uint32_t)((i + j) * OZ_BN);
+            const int acc_idx = (i + j) < NACC ? (i + j) : NACC - 1;
+            const uint32_t d_tmem = tmem + (uint32_t)(acc_idx * OZ_BN);
 #pragma unroll
             for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-              const uint32_t accum = (first_in_chunk && i == 0 && kk == 0) ? 0u : 1u;
+              // the first write of accumulator a in a chunk is the pair (0, a), kk = 0
+              const uint32_t accum = (first_in_chunk && i == 0 && kk == 0 && j < NACC) ? 0u : 1u;
               mma_bf16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc, accum);
             }
           }
@@ -266,9 +270,9 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
       for (int blk = 0; blk < 4; ++blk) {
         const int c0 = h * 64 + blk * 16;
-        float D[S][16];
+        float D[NACC][16];
 #pragma unroll
-        for (int d = 0; d < S; ++d)
+        for (int d = 0; d < NACC; ++d)
           tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * OZ_BN + c0), D[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (gr < p.M) {
@@ -277,9 +281,10 @@ __global__ void __launch_bounds__(320, 1)
           for (int c = 0; c < 16; ++c) {
             const int gc = n0 + c0 + c;
             if (gc >= p.N || (p.lower_elems && gc > gr)) continue;
+            // slices carry their 2^(-7i) scale, so the groups add directly
             df v = df_make(D[0][c], 0.f);
 #pragma unroll
-            for (int d = 1; d < S; ++d) v = df_add_f(v, D[d][c] * pow2f(-7 * d));
+            for (int d = 1; d < NACC; ++d) v = df_add_f(v, D[d][c]);
             const int eb = eB[(int64_t)chunk * p.expB_chunk_stride + gc];
             v = df_scale(v, pow2f(ea + eb - 14));
             if (p.beta < 0.f) v = df_neg(v);
@@ -334,7 +339,8 @@ __device__ __forceinline__ void slice_and_store(const df (&x)[8], int e, uint16_
       // remainder (exact): (hi - v) + lo, then scaled by 2^7 for the next slice
       df rem = df_add_f(df_make(r[i].hi - v, 0.f), r[i].lo);
       r[i] = df_scale(rem, 128.f);
-      const __nv_bfloat16 bv = __float2bfloat16_rn(v);
+      // slice s is stored as v_s 2^(-7s) (exact: a power-of-two scaling of an integer <= 2^8)
+      const __nv_bfloat16 bv = __float2bfloat16_rn(v * pow2f(-7 * s));
       out[i] = *reinterpret_cast<const uint16_t*>(&bv);
     }
     if (valid) {
@@ -462,7 +468,7 @@ static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs&
   }
   const int tiles = a.lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
   if (tiles <= 0) return INLA_OK;
-  count_launch(), k_ozaki_gemm<S><<<dim3(tiles, 1, nslots), 320, smem, st>>>(ma, mb, a);
+  count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S><<<dim3(tiles, 1, nslots), 320, smem, st>>>(ma, mb, a);
   if (debug_sync_enabled()) {
     char site[200];
     snprintf(site, sizeof(site), "ozaki S=%d M=%d N=%d K=%d kmode=%d lower=%d slots=%d", S, a.M, a.N, a.K, a.k_mode,
@@ -534,6 +540,7 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
     case 2: rc = launch_oz<2>(ma, mb, a, nslots, st); break;
     case 3: rc = launch_oz<3>(ma, mb, a, nslots, st); break;
     case 4: rc = launch_oz<4>(ma, mb, a, nslots, st); break;
+    case 5: rc = launch_oz<5>(ma, mb, a, nslots, st); break;
     default: rc = INLA_E_BADARG;
   }
   if (g_stats.on) {
@@ -584,9 +591,9 @@ static void slice_impl(const T* src, int64_t sss, int ld, int row0, int col0, in
   const int nchunks = (K + OZ_CHUNK - 1) / OZ_CHUNK;
   if (!transposed) {
     const int64_t warps = (int64_t)R * nchunks;
-    count_launch(), k_slice_rows<T><<<dim3((unsigned)((warps + 7) / 8), nslots), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    count_launch("k_slice_rows<T>"), k_slice_rows<T><<<dim3((unsigned)((warps + 7) / 8), nslots), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   } else {
-    count_launch(), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   }
   if (debug_sync_enabled()) {
     char site[200];

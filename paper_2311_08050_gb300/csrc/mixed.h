@@ -36,7 +36,9 @@ struct Batch {
   int64_t mat_stride, z_stride, s_stride, linv_stride, wd_stride, slinv_stride;
   // mixed-path workspace
   bool mixed;
-  int S;
+  int S;                 // slices of the GEMMs being issued (set per phase)
+  int S_exact = 0;       // prior inversion and the factor at the mode
+  int S_newton = 0;      // Newton-step factorisations
   uint16_t *PA, *PB, *PBIG;
   int32_t *EA, *EB, *EBIG;
   int64_t pa_cap, pb_cap, pbig_cap;   // elements per slot

@@ -19,7 +19,14 @@ constexpr int OZ_BM = 128;      // tile rows (tcgen05 M)
 constexpr int OZ_BN = 128;      // tile columns (tcgen05 N)
 constexpr int OZ_BK = 64;       // K per TMA box (128-byte swizzle of BF16)
 constexpr int OZ_CHUNK = 256;   // K per exact accumulation chunk (one exponent per row)
-constexpr int OZ_MAX_S = 4;
+constexpr int OZ_MAX_S = 5;
+// TMEM accumulators per tile (4 x 128 columns = all 512).  Slice i is stored pre-scaled by
+// 2^(-7i), so a product V_i W_j^T arrives with its weight 2^(-7(i+j)): groups d = 0, 1, 2 are
+// exact in FP32 (integers times 2^(-7d) with < 24 significant bits over a 256-wide chunk) and
+// every group d >= 3 is summed into the fourth accumulator, where FP32 rounding costs
+// ~2^-24 of a 2^-21-scaled quantity, i.e. ~2^-45 of the product: negligible against the
+// 2^-7S slice truncation.
+constexpr int OZ_NACC = 4;
 
 // A sliced operand: planes [plane = slot * S + slice][row][k] (BF16, row stride ld_k
 // elements, plane stride plane_stride elements) and exponents [slot][chunk][row] (int32,

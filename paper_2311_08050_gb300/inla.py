@@ -51,7 +51,8 @@ class ModelDesc(C.Structure):
 
 
 class Opts(C.Structure):
-    _fields_ = [("precision", _i32), ("slices", _i32), ("newton_tol", _d), ("newton_max", _i32),
+    _fields_ = [("precision", _i32), ("slices", _i32), ("newton_slices", _i32), ("newton_tol", _d),
+                ("newton_max", _i32),
                 ("spin_limit", _i64), ("stream", C.c_void_p), ("flags", _i32)]
 
 
@@ -93,11 +94,12 @@ def _ptr(a, ct):
 
 
 def make_opts(precision="fp64", slices=0, newton_tol=1e-8, newton_max=50, stream=None, device_out=False,
-              spin_limit=1 << 26):
+              spin_limit=1 << 26, newton_slices=0):
     o = Opts()
     lib().inla_opts_default(C.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.slices = slices
+    o.newton_slices = newton_slices
     o.newton_tol = newton_tol
     o.newton_max = newton_max
     o.spin_limit = spin_limit

@@ -43,7 +43,7 @@ def _bound(A, Bm, S, K):
     return (S + 2) * 2.0 ** (-7 * S) * K * ra * rb + 1e-13 * np.abs(A) @ np.abs(Bm).T
 
 
-@pytest.mark.parametrize("S", [2, 3, 4])
+@pytest.mark.parametrize("S", [2, 3, 4, 5])
 def test_plain_product_within_slice_bound(lib, S):
     rng = np.random.default_rng(S)
     M, N, K = 300, 260, 320          # ragged tiles, K = one full chunk + a partial one
