@@ -157,6 +157,24 @@ int inla_marginals(inla_model *model, const double *theta, const inla_opts *opts
 /* Static text for a status code. */
 const char *inla_status_string(int status);
 
+/* Allocation-free Ozaki-split tensor-core product C = A B^T (the paper has no counterpart:
+ * this is a building block of the mixed path offered on its own).  For callers that cannot
+ * call cudaMalloc -- an application that reserves all device memory up front in its own pool
+ * and hands out only pointers into it, or code that must not risk the device-wide
+ * synchronisation and out-of-memory failure of an allocation mid-work.
+ *  A: M x K, B: N x K, C: M x N, row-major FP64 DEVICE pointers on the current device,
+ *  caller-owned (inputs read, C overwritten).  M, N, K <= 512, K a multiple of 64,
+ *  slices in 2..5; otherwise INLA_E_BADARG.  stream: cudaStream_t or NULL.
+ *  Every intermediate lives in one static device array of ~7.4 MB that each GPU loading the
+ *  library holds until the process exits; the call allocates nothing (no cudaMalloc, no
+ *  library allocator).  The first call on a device looks that array's address up
+ *  (cudaGetSymbolAddress), so make it before any stream capture.  All calls share the array
+ *  and it keeps the last call's contents: calls that overlap on the GPU (other streams,
+ *  other host threads) race.  The call synchronizes `stream` before returning;
+ *  INLA_E_TIMEOUT if a bounded device-side wait gave up. */
+int inla_ozaki_gemm_noalloc(const double *A, const double *B, double *C, int32_t M, int32_t N, int32_t K,
+                            int32_t slices, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
