@@ -303,6 +303,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_gemm(args):
+    """Microbenchmark of the Ozaki GEMM alone (test hook): tensor-pipe and algorithmic rates
+    for the shapes given as M,N,K,S[,lower] separated by ';'."""
+    from paper_2311_08050_gb300 import build as B
+    from paper_2311_08050_gb300 import inla
+    B.build()
+    L = inla.lib()
+    P = C.POINTER(C.c_double)
+    L.inla_test_ozaki_gemm.argtypes = [P, P, P] + [C.c_int32] * 8 + [C.c_double, C.c_double]
+    L.inla_test_stats_read.argtypes = [C.POINTER(C.c_double)]
+    peaks, _ = _peaks()
+    rng = np.random.default_rng(0)
+    res = []
+    for spec in args.gemm.split(";"):
+        f = [int(x) for x in spec.split(",")]
+        M, N, K, S = f[:4]
+        lower = f[4] if len(f) > 4 else 0
+        accumulate = f[5] if len(f) > 5 else 0    # C = C - A B^T instead of C = A B^T
+        A = rng.standard_normal((M, K))
+        Bm = rng.standard_normal((N, K))
+        Cm = np.zeros((M, N))
+        for rep in range(3):
+            L.inla_test_stats_enable(1 if rep == 2 else 0)
+            rc = L.inla_test_ozaki_gemm(A.ctypes.data_as(P), Bm.ctypes.data_as(P), Cm.ctypes.data_as(P), M, N, K, S,
+                                        0, 0, lower, 0, 1.0 if accumulate else 0.0, -1.0 if accumulate else 1.0)
+            assert rc == 0
+        L.inla_test_stats_enable(0)
+        st = (C.c_double * 4)()
+        L.inla_test_stats_read(st)
+        ms = st[3]
+        tens = st[2] / (ms / 1e3) / 1e12
+        res.append({"M": M, "N": N, "K": K, "S": S, "lower": lower, "accumulate": accumulate, "ms": ms, "tensor_tflops": tens,
+                    "alg_tflops": st[1] / (ms / 1e3) / 1e12, "frac_bf16_burst": tens / peaks["bf16_tflops"]})
+    print(json.dumps({"gemm_microbench": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,7 +354,11 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--config", type=int, default=5, choices=[5, 2, 1],
                     help="5: the benchmark workload; 2 / 1: smaller cases for profiling captures")
+    ap.add_argument("--gemm", default=None, help="microbenchmark the Ozaki GEMM: 'M,N,K,S[,lower[,accumulate]];...'")
     args = ap.parse_args()
+    if args.gemm:
+        run_gemm(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -34,6 +34,12 @@ bool debug_sync_enabled() {
   }
   return on == 1;
 }
+int note_launch_error(const char* site) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return INLA_OK;
+  if (!g_debug_site[0]) snprintf(g_debug_site, sizeof(g_debug_site), "%s: %s", site, cudaGetErrorString(e));
+  return INLA_E_CUDA;
+}
 int debug_check(cudaStream_t st, const char* site) {
   if (!debug_sync_enabled()) return INLA_OK;
   cudaError_t e = cudaStreamSynchronize(st);

@@ -144,6 +144,8 @@ namespace inla {
 // stream and records the first site at which a CUDA error became visible.
 bool debug_sync_enabled();
 int debug_check(cudaStream_t st, const char* site);
+// INLA_OK, or INLA_E_CUDA after recording `site` and the pending launch error (which it clears)
+int note_launch_error(const char* site);
 // number of kernels this library has launched (read and reset by inla_test_launch_count)
 extern int64_t g_kernel_launches;
 // called before every kernel launch: counts it and, while the profiler is on, records a CUDA

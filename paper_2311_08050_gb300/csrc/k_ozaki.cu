@@ -1,13 +1,17 @@
 // tcgen05 / TMA implementation of the Ozaki-split GEMM declared in ozaki.h.
 //
-// One CTA computes one 128 x 128 output tile with 10 warps:
-//   warp 0      TMA producer: B slices of a 64-wide K step stay resident (2 stages),
-//               A slices stream through a 2-stage ring;
+// Persistent kernel: one CTA per SM walks 128 x 128 output tiles (slot-major) with 12 warps
+// (warpgroup 0 gives registers up to warpgroups 1-2 with setmaxnreg):
+//   warp 0      TMA producer: a stage is the S slices of A and of B for 32 values of k
+//               (two 3-D boxes, 64-byte swizzle); 2..6 stages depending on S;
 //   warp 1      owns the TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=128, K=16,
-//               BF16 x BF16 -> FP32) into S accumulators, one per slice-order d = i + j;
-//   warps 2..9  epilogue: after each 256-wide K chunk, read the accumulators (tcgen05.ld),
-//               combine them exactly in double-float, scale by 2^(eA + eB - 14) and add the
-//               chunk into C (double-float) in global memory.
+//               BF16 x BF16 -> FP32) into min(S, 4) accumulators, slice-order d = i + j
+//               (groups d >= 3 share the last one);
+//   warps 4..11 epilogue: after each 256-wide K chunk, read the accumulators (tcgen05.ld),
+//               combine them in double-float, scale by 2^(eA + eB - 14) and add the chunk
+//               into a register tile, then release the TMEM so that the next chunk (or tile)
+//               runs on the tensor cores while the finished tile is added into C (double-float,
+//               global) with coalesced row segments.
 // Every mbarrier wait is bounded by spin_limit; on a timeout the CTA records the failure in
 // *err, stops issuing work, drains what it issued and returns.
 #include <cudaTypedefs.h>
@@ -52,11 +56,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
-         ((uint64_t)2 << 61);
-}
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
@@ -67,80 +66,103 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// Pipeline geometry: a stage holds the S slices of both operands for OZ_KS values of k;
+// the stage count fills the shared memory left after the epilogue staging buffers.
+template <int S>
+struct OzCfg {
+  static constexpr int STAGE_BYTES = 2 * S * OZ_SLICE_BYTES;
+  static constexpr int NST_FIT = (OZ_SMEM_BUDGET - 1024 - OZ_STAGING_BYTES) / STAGE_BYTES;
+  static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
+  static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OZ_STAGING_BYTES;  // 1024: alignment slack
+  static constexpr int NACC = S < OZ_NACC ? S : OZ_NACC;
+  static constexpr uint32_t TMEM_COLS = NACC * OZ_BN <= 256 ? 256 : 512;
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-constexpr int A_BYTES = OZ_BM * OZ_BK * 2;  // 16 KB
-constexpr int B_BYTES = OZ_BN * OZ_BK * 2;  // 16 KB
-
-__device__ __forceinline__ void tile_coords(const OzArgs& p, int& tm, int& tn) {
-  const int x = blockIdx.x;
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)4 << 61);
+}
+// Double-float sum without the second error-free step on the low words: its error, ~2^-44 of
+// |a| + |b|, stays far below the slice truncation of the products it accumulates.
+__device__ __forceinline__ float2 df2_add_fast(float2 a, float2 b) {
+  float s, t;
+  two_sum(a.x, b.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+  fast_two_sum(s, t, s, t);
+  return make_float2(s, t);
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// Tile t of the launch (slots outermost): its slot, origin and K range in 32-wide stages.
+struct OzTile {
+  int slot, m0, n0, k_lo, n_st;
+};
+__device__ __forceinline__ OzTile oz_tile(const OzArgs& p, int t) {
+  OzTile r;
+  r.slot = t / p.tiles_per_slot;
+  const int x = t - r.slot * p.tiles_per_slot;
+  int tm, tn;
   if (p.lower) {
-    int t = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
-    while (t * (t + 1) / 2 > x) --t;
-    while ((t + 1) * (t + 2) / 2 <= x) ++t;
-    tm = t;
-    tn = x - t * (t + 1) / 2;
+    int u = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+    while (u * (u + 1) / 2 > x) --u;
+    while ((u + 1) * (u + 2) / 2 <= x) ++u;
+    tm = u;
+    tn = x - u * (u + 1) / 2;
   } else {
     tm = x / p.tiles_n;
-    tn = x % p.tiles_n;
+    tn = x - tm * p.tiles_n;
   }
+  r.m0 = tm * OZ_BM;
+  r.n0 = tn * OZ_BN;
+  int k_lo = 0;
+  if (p.k_mode == 1) k_lo = max(r.m0, r.n0);
+  else if (p.k_mode == 2) k_lo = r.n0;
+  else if (p.k_mode == 3) k_lo = r.m0;
+  k_lo = (k_lo / OZ_BK) * OZ_BK;
+  r.k_lo = k_lo;
+  r.n_st = k_lo < p.K ? (p.K - k_lo) / OZ_KS : 0;
+  return r;
 }
 
 }  // namespace
 
 template <int S>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzArgs p) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  using Cfg = OzCfg<S>;
+  constexpr int NST = Cfg::NST, NACC = Cfg::NACC;
+  constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
+  extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Bbuf = smem;                       // 2 stages x S slices x 16 KB
-  uint8_t* Abuf = smem + 2 * S * B_BYTES;     // 2 stages x 16 KB
-  __shared__ __align__(8) uint64_t fullB[2], emptyB[2], fullA[2], emptyA[2], acc_full, acc_empty, done_bar;
+  float2* staging = reinterpret_cast<float2*>(smem + NST * STAGE_BYTES);
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full, acc_empty, done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh_;
   volatile int& abort_sh = abort_sh_;
-
-  int tm, tn;
-  tile_coords(p, tm, tn);
-  if (tm >= p.tiles_m || tn >= p.tiles_n) return;
-  const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-  const int slot = blockIdx.z;
-  int k_lo = 0;
-  if (p.k_mode == 1) k_lo = max(m0, n0);
-  else if (p.k_mode == 2) k_lo = n0;
-  else if (p.k_mode == 3) k_lo = m0;
-  k_lo = (k_lo / OZ_BK) * OZ_BK;
-  const int n_kc = k_lo < p.K ? (p.K - k_lo) / OZ_BK : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&fullB[s], 1);
-      mbar_init(&emptyB[s], 1);
-      mbar_init(&fullA[s], 1);
-      mbar_init(&emptyA[s], 1);
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
     mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 256);
+    mbar_init(&acc_empty, OZ_EPI_WARPS * 32);
     mbar_init(&done_bar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // slice-order groups d = i + j >= NACC-1 share the last accumulator (see ozaki.h)
-  constexpr int NACC = S < OZ_NACC ? S : OZ_NACC;
-  constexpr uint32_t TMEM_COLS = NACC * OZ_BN <= 256 ? 256 : 512;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "n"(TMEM_COLS));
+                 "n"(Cfg::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -151,162 +173,237 @@ __global__ void __launch_bounds__(320, 1)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    if (lane == 0 && n_kc > 0) {
-      int issued_b = 0, issued_a = 0;
-      for (int kc = 0; kc < n_kc && !abort_sh; ++kc) {
-        const int k = k_lo + kc * OZ_BK;
-        const int b = kc & 1;
-        if (kc >= 2 && !mbar_wait(&emptyB[b], ((kc >> 1) - 1) & 1, lim)) {
-          abort_sh = 1;
-          break;
-        }
-        mbar_expect_tx(&fullB[b], S * B_BYTES);
-        for (int j = 0; j < S; ++j) tma_load_3d(Bbuf + (b * S + j) * B_BYTES, &tmB, k, n0, slot * S + j, &fullB[b]);
-        issued_b = kc + 1;
-        for (int i = 0; i < S; ++i) {
-          const int a = kc * S + i, sa = a & 1;
-          if (a >= 2 && !mbar_wait(&emptyA[sa], ((a >> 1) - 1) & 1, lim)) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_ROLE_REGS));
+    // one stage = the S slices of A and of B for 32 values of k (two 3-D boxes)
+    if (lane == 0) {
+      int g = 0;  // stages issued by this CTA
+      for (int t = blockIdx.x; t < p.tiles_total && !abort_sh; t += gridDim.x) {
+        const OzTile ti = oz_tile(p, t);
+        for (int s = 0; s < ti.n_st; ++s, ++g) {
+          const int st = g % NST, u = g / NST;
+          if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1, lim)) {
             abort_sh = 1;
             break;
           }
-          mbar_expect_tx(&fullA[sa], A_BYTES);
-          tma_load_3d(Abuf + sa * A_BYTES, &tmA, k, m0, slot * S + i, &fullA[sa]);
-          issued_a = a + 1;
+          uint8_t* dst = smem + st * STAGE_BYTES;
+          const int k = ti.k_lo + s * OZ_KS;
+          mbar_expect_tx(&full[st], STAGE_BYTES);
+          tma_load_3d(dst, &tmA, k, ti.m0, ti.slot * S, &full[st]);
+          tma_load_3d(dst + S * OZ_SLICE_BYTES, &tmB, k, ti.n0, ti.slot * S, &full[st]);
         }
       }
       if (abort_sh) {
         // drain the copies already issued before leaving (bounded)
-        for (int kc = max(0, issued_b - 2); kc < issued_b; ++kc) mbar_wait(&fullB[kc & 1], (kc >> 1) & 1, lim);
-        for (int a = max(0, issued_a - 2); a < issued_a; ++a) mbar_wait(&fullA[a & 1], (a >> 1) & 1, lim);
+        for (int h = max(0, g - NST); h < g; ++h) mbar_wait(&full[h % NST], (h / NST) & 1, lim);
         atomicExch(p.err, 1);
       }
     }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
-    if (lane == 0 && n_kc > 0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_ROLE_REGS));
+    if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
                              ((uint32_t)(OZ_BM >> 4) << 24);
-      int chunk_no = 0;
-      bool first_in_chunk = true;
-      for (int kc = 0; kc < n_kc && !abort_sh; ++kc) {
-        const int k = k_lo + kc * OZ_BK;
-        if (first_in_chunk && chunk_no > 0) {
-          if (!mbar_wait(&acc_empty, (chunk_no - 1) & 1, lim)) {
-            abort_sh = 1;
-            break;
+      int g = 0, c = 0;  // stages consumed, chunks completed
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.tiles_total && ok && !abort_sh; t += gridDim.x) {
+        const OzTile ti = oz_tile(p, t);
+        bool first_in_chunk = true;
+        for (int s = 0; s < ti.n_st; ++s, ++g) {
+          const int k = ti.k_lo + s * OZ_KS;
+          if (first_in_chunk && c > 0) {
+            // the epilogue has read the previous chunk out of the accumulators
+            if (!mbar_wait(&acc_empty, (c - 1) & 1, lim)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
           }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-        }
-        const int b = kc & 1;
-        if (!mbar_wait(&fullB[b], (kc >> 1) & 1, lim)) {
-          abort_sh = 1;
-          break;
-        }
-        bool ok = true;
-        for (int i = 0; i < S; ++i) {
-          const int a = kc * S + i, sa = a & 1;
-          if (!mbar_wait(&fullA[sa], (a >> 1) & 1, lim)) {
+          const int st = g % NST, u = g / NST;
+          if (!mbar_wait(&full[st], u & 1, lim)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a_addr = smem_u32(Abuf + sa * A_BYTES);
-          for (int j = 0; j < S - i; ++j) {
-            const uint32_t b_addr = smem_u32(Bbuf + (b * S + j) * B_BYTES);
-            const int acc_idx = (i + j) < NACC ? (i + j) : NACC - 1;
-            const uint32_t d_tmem = tmem + (uint32_t)(acc_idx * OZ_BN);
+          const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-              // the first write of accumulator a in a chunk is the pair (0, a), kk = 0
-              const uint32_t accum = (first_in_chunk && i == 0 && kk == 0 && j < NACC) ? 0u : 1u;
-              mma_bf16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc, accum);
+          for (int i = 0; i < S; ++i) {
+#pragma unroll
+            for (int j = 0; j < S - i; ++j) {
+              const int acc_idx = (i + j) < NACC ? (i + j) : NACC - 1;
+              const uint32_t d_tmem = tmem + (uint32_t)(acc_idx * OZ_BN);
+              const uint32_t a_addr = base + i * OZ_SLICE_BYTES, b_addr = base + (S + j) * OZ_SLICE_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < OZ_KS / 16; ++kk) {
+                // the first write of accumulator a in a chunk is the pair (0, a), kk = 0
+                const uint32_t accum = (first_in_chunk && i == 0 && kk == 0 && j < NACC) ? 0u : 1u;
+                mma_bf16(d_tmem, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32), idesc, accum);
+              }
             }
           }
-          mma_commit(&emptyA[sa]);
-        }
-        if (!ok) {
-          abort_sh = 1;
-          break;
-        }
-        mma_commit(&emptyB[b]);
-        first_in_chunk = false;
-        const bool chunk_end = ((k + OZ_BK) % OZ_CHUNK == 0) || (kc == n_kc - 1);
-        if (chunk_end) {
-          mma_commit(&acc_full);
-          ++chunk_no;
-          first_in_chunk = true;
+          mma_commit(&empty[st]);
+          first_in_chunk = false;
+          if (((k + OZ_KS) % OZ_CHUNK) == 0 || s == ti.n_st - 1) {
+            mma_commit(&acc_full);
+            ++c;
+            first_in_chunk = true;
+          }
         }
       }
       // all issued MMAs complete before the TMEM is released
       mma_commit(&done_bar);
       mbar_wait(&done_bar, 0, lim);
-      if (abort_sh) atomicExch(p.err, 1);
-    }
-  } else {
-    // ------------------------------ epilogue ------------------------------
-    const int q = warp & 3, h = (warp - 2) >> 2;
-    const int row = q * 32 + lane;
-    const int gr = m0 + row;
-    const int32_t* eA = p.expA + slot * p.expA_slot_stride;
-    const int32_t* eB = p.expB + slot * p.expB_slot_stride;
-    float2* C = p.C + slot * p.C_slot_stride;
-    if (n_kc == 0 && p.alpha == 0.f && gr < p.M)
-      for (int c = h * 64; c < h * 64 + 64; ++c) {
-        const int gc = n0 + c;
-        if (gc < p.N && !(p.lower_elems && gc > gr)) df_store(C + (int64_t)gr * p.ldc + gc, df_make(0.f, 0.f));
-      }
-    int chunk_no = 0;
-    for (int k = k_lo; k < p.K && !abort_sh;) {
-      const int k_end = min(p.K, (k / OZ_CHUNK + 1) * OZ_CHUNK);
-      const int chunk = k / OZ_CHUNK;
-      if (!mbar_wait(&acc_full, chunk_no & 1, lim)) {
+      if (!ok || abort_sh) {
         abort_sh = 1;
         atomicExch(p.err, 1);
-        break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int ea = gr < p.M ? eA[(int64_t)chunk * p.expA_chunk_stride + gr] : 0;
-      const bool first = (chunk_no == 0);
-#pragma unroll 1
-      for (int blk = 0; blk < 4; ++blk) {
-        const int c0 = h * 64 + blk * 16;
-        float D[NACC][16];
+    }
+  } else if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_ROLE_REGS));
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    // Thread = one row of the tile and 64 columns (warp half h).  Per chunk: drain the group
+    // accumulators into a double-float register tile and release the TMEM, so that the next
+    // chunk's (or tile's) MMAs start at once.  After the tile's last chunk, add the tile into C
+    // through a per-warp staging buffer: each store instruction writes 64-byte row segments.
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(OZ_EPI_REGS));
+    const int ew = warp - 4;
+    const int q = warp & 3, h = ew >> 2;
+    const int row = q * 32 + lane;
+    float2* stg = staging + ew * (32 * OZ_STG_LD);
+    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
+    const bool neg = p.beta < 0.f;
+    const bool accumulate = p.alpha != 0.f;
+    constexpr float kRound = 12582912.f;  // 1.5 * 2^23
+    int c = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.tiles_total && ok; t += gridDim.x) {
+      const OzTile ti = oz_tile(p, t);
+      const int gr = ti.m0 + row;
+      const int col0 = ti.n0 + h * 64;
+      float2* C = p.C + ti.slot * p.C_slot_stride;
+      float2 acc[64];
+      if (ti.n_st == 0) {
+        if (p.alpha != 0.f) continue;
 #pragma unroll
-        for (int d = 0; d < NACC; ++d)
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * OZ_BN + c0), D[d]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (gr < p.M) {
-          float2* crow = C + (int64_t)gr * p.ldc + n0 + c0;
+        for (int j = 0; j < 64; ++j) acc[j] = make_float2(0.f, 0.f);
+      } else {
+        if (p.alpha != 0.f && gr < p.M)
+          for (int j = 0; j < 64; j += 16)
+            if (col0 + j < p.N) prefetch_l2(C + (int64_t)gr * p.ldc + col0 + j);
+        const int32_t* eA = p.expA + ti.slot * p.expA_slot_stride;
+        const int32_t* eB = p.expB + ti.slot * p.expB_slot_stride;
+        for (int k = ti.k_lo; k < p.K;) {
+          const int chunk = k / OZ_CHUNK;
+          const int k_end = min(p.K, (chunk + 1) * OZ_CHUNK);
+          // scales of this chunk: +-2^(eA - 14) for the thread's row (sign of beta); 2^eB for
+          // columns lane and lane + 32, shuffled to the other lanes
+          float rs = pow2f(gr < p.M ? eA[(int64_t)chunk * p.expA_chunk_stride + gr] - 14 : 0);
+          if (neg) rs = -rs;
+          const int64_t eb_base = (int64_t)chunk * p.expB_chunk_stride;
+          const float cs0 = pow2f(col0 + lane < p.N ? eB[eb_base + col0 + lane] : 0);
+          const float cs1 = pow2f(col0 + 32 + lane < p.N ? eB[eb_base + col0 + 32 + lane] : 0);
+          bool got = mbar_wait(&acc_full, c & 1, lim);
+          got = __all_sync(0xffffffffu, got);
+          if (!got) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const bool first = (k == ti.k_lo);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int gc = n0 + c0 + c;
-            if (gc >= p.N || (p.lower_elems && gc > gr)) continue;
-            // slices carry their 2^(-7i) scale, so the groups add directly
-            df v = df_make(D[0][c], 0.f);
+          for (int blk = 0; blk < 8; ++blk) {
+            float D[NACC][8];
 #pragma unroll
-            for (int d = 1; d < NACC; ++d) v = df_add_f(v, D[d][c]);
-            const int eb = eB[(int64_t)chunk * p.expB_chunk_stride + gc];
-            v = df_scale(v, pow2f(ea + eb - 14));
-            if (p.beta < 0.f) v = df_neg(v);
-            if (first && p.alpha == 0.f) {
-              df_store(crow + c, v);
-            } else {
-              df_store(crow + c, df_add(df_load(crow + c), v));
+            for (int d = 0; d < NACC; ++d) tmem_ld8(t_lane + (uint32_t)(d * OZ_BN + h * 64 + blk * 8), D[d]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int d = 0; d < NACC; ++d)
+#pragma unroll
+              for (int cc = 0; cc < 8; ++cc) asm volatile("" : "+f"(D[d][cc]));
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+              const int j = blk * 8 + cc;
+              // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14
+              // below 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the
+              // fractions exactly into the low word (multiples of 2^-14 below 1), and the
+              // rounded tail group (d >= 3) costs ~2^-24 of a value below 2^4.
+              // (Integer parts by the 1.5 * 2^23 shift, exact for |x| < 2^22, on the FP32 pipe.)
+              float s = D[0][cc], e = 0.f;
+              {
+                const float t = __fsub_rn(__fadd_rn(D[1][cc], kRound), kRound);
+                s = __fadd_rn(s, t);
+                e = __fsub_rn(D[1][cc], t);
+              }
+              if (NACC >= 3) {
+                const float t = __fsub_rn(__fadd_rn(D[2][cc], kRound), kRound);
+                s = __fadd_rn(s, t);
+                e = __fadd_rn(e, __fsub_rn(D[2][cc], t));
+              }
+              if (NACC >= 4) e = __fadd_rn(e, D[NACC - 1][cc]);
+              const float sc = rs * __shfl_sync(0xffffffffu, j < 32 ? cs0 : cs1, j & 31);
+              if (first) {
+                acc[j] = make_float2(s * sc, e * sc);
+              } else {
+                acc[j] = df2_add_fast(acc[j], make_float2(s * sc, e * sc));
+              }
             }
           }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(&acc_empty);
+          ++c;
+          k = k_end;
+        }
+        if (!ok) break;
+      }
+      // C update through the staging buffer, 8 columns at a time: 8 lanes per row segment
+      const int cc = lane & 7;
+      int grow[8];
+      float2* crow[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        grow[i] = ti.m0 + q * 32 + i * 4 + (lane >> 3);
+        crow[i] = C + (int64_t)grow[i] * p.ldc;
+      }
+#pragma unroll
+      for (int blk = 0; blk < 8; ++blk) {
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) stg[lane * OZ_STG_LD + u] = acc[blk * 8 + u];
+        __syncwarp();
+        const int gcol = col0 + blk * 8 + cc;
+        bool valid[8];
+        float2 old[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          valid[i] = grow[i] < p.M && gcol < p.N && !(p.lower_elems && gcol > grow[i]);
+          old[i] = make_float2(0.f, 0.f);
+          if (accumulate && valid[i]) old[i] = __ldcg(crow[i] + gcol);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float2 v = stg[(i * 4 + (lane >> 3)) * OZ_STG_LD + cc];
+          if (accumulate) {
+            v = df2_add_fast(old[i], v);
+          } else {
+            float hi, lo;
+            two_sum(v.x, v.y, hi, lo);
+            v = make_float2(hi, lo);
+          }
+          if (valid[i]) crow[i][gcol] = v;
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mbar_arrive(&acc_empty);
-      ++chunk_no;
-      k = k_end;
+    }
+    if (!ok) {
+      abort_sh = 1;
+      atomicExch(p.err, 1);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(Cfg::TMEM_COLS));
   }
 }
 
@@ -444,31 +541,47 @@ static int get_encode() {
   return INLA_OK;
 }
 
-int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes) {
+int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S) {
   INLA_TRY(get_encode());
-  if ((op.ld_k % OZ_BK) != 0 || (op.K % OZ_BK) != 0 || ((uintptr_t)op.planes & 15) != 0) return INLA_E_BADARG;
+  if ((op.ld_k % OZ_BK) != 0 || (op.K % OZ_BK) != 0 || ((uintptr_t)op.planes & 15) != 0 || S < 1 ||
+      S > OZ_MAX_S || nplanes % S)
+    return INLA_E_BADARG;
   cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)op.ld_k * 2, (cuuint64_t)op.plane_stride * 2};
-  cuuint32_t box[3] = {OZ_BK, OZ_BM, 1};
+  cuuint32_t box[3] = {OZ_KS, OZ_BM, (cuuint32_t)S};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.planes, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? INLA_OK : INLA_E_BADARG;
 }
 
+static int num_sms() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+// Persistent launch: one CTA per SM (shared memory allows no second), tiles round-robin.
 template <int S>
 static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs& a, int nslots, cudaStream_t st) {
-  const int smem = 2 * S * B_BYTES + 2 * A_BYTES + 1024;
+  constexpr int smem = OzCfg<S>::SMEM;
   static bool init = false;
   if (!init) {
     if (cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return INLA_E_CUDA;
     init = true;
   }
-  const int tiles = a.lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
-  if (tiles <= 0) return INLA_OK;
-  count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S><<<dim3(tiles, 1, nslots), 320, smem, st>>>(ma, mb, a);
+  if (a.tiles_total <= 0) return INLA_OK;
+  const int grid = std::min(a.tiles_total, num_sms());
+  count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S><<<grid, OZ_THREADS, smem, st>>>(ma, mb, a);
+  if (cudaPeekAtLastError() != cudaSuccess) return note_launch_error("k_ozaki_gemm launch");
   if (debug_sync_enabled()) {
     char site[200];
     snprintf(site, sizeof(site), "ozaki S=%d M=%d N=%d K=%d kmode=%d lower=%d slots=%d", S, a.M, a.N, a.K, a.k_mode,
@@ -526,9 +639,11 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
   a.expB_slot_stride = B.exp_slot_stride;
   a.tiles_m = (a.M + OZ_BM - 1) / OZ_BM;
   a.tiles_n = (a.N + OZ_BN - 1) / OZ_BN;
+  a.tiles_per_slot = a.lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  a.tiles_total = a.tiles_per_slot * nslots;
   CUtensorMap ma, mb;
-  INLA_TRY(oz_make_map(&ma, A, a.S * nslots));
-  INLA_TRY(oz_make_map(&mb, B, a.S * nslots));
+  INLA_TRY(oz_make_map(&ma, A, a.S * nslots, a.S));
+  INLA_TRY(oz_make_map(&mb, B, a.S * nslots, a.S));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (g_stats.on) {
     cudaEventCreate(&e0);

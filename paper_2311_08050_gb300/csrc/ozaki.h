@@ -17,9 +17,23 @@ namespace inla {
 
 constexpr int OZ_BM = 128;      // tile rows (tcgen05 M)
 constexpr int OZ_BN = 128;      // tile columns (tcgen05 N)
-constexpr int OZ_BK = 64;       // K per TMA box (128-byte swizzle of BF16)
+constexpr int OZ_BK = 64;       // K granularity of operands and of the k ranges
+constexpr int OZ_KS = 32;       // K per pipeline stage (64-byte swizzled rows of BF16)
 constexpr int OZ_CHUNK = 256;   // K per exact accumulation chunk (one exponent per row)
 constexpr int OZ_MAX_S = 5;
+constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_KS * 2;   // one slice of one operand for one stage
+constexpr int OZ_EPI_WARPS = 8;                     // epilogue warps (two per TMEM lane quarter)
+constexpr int OZ_THREADS = 384;                     // warpgroup 0: TMA + MMA; 1-2: epilogue
+// Register split: launched at 168 per thread (384 x 168 <= 64K; three warps share each
+// sub-partition's 16K registers), then warpgroup 0 drops to OZ_ROLE_REGS and the epilogue
+// warpgroups rise to OZ_EPI_REGS, which holds a finished 128 x 128 double-float tile in
+// registers (64 columns per thread).  4 * 56 + 8 * 224 = 12 * 168.
+constexpr int OZ_ROLE_REGS = 56;
+constexpr int OZ_EPI_REGS = 224;
+static_assert(4 * OZ_ROLE_REGS + 8 * OZ_EPI_REGS <= 12 * 168, "register split exceeds the launch allocation");
+constexpr int OZ_STG_LD = 9;                        // epilogue staging row stride (float2)
+constexpr int OZ_STAGING_BYTES = OZ_EPI_WARPS * 32 * OZ_STG_LD * 8;
+constexpr int OZ_SMEM_BUDGET = 232448 - 512;        // opt-in maximum less the static barriers
 // TMEM accumulators per tile (4 x 128 columns = all 512).  Slice i is stored pre-scaled by
 // 2^(-7i), so a product V_i W_j^T arrives with its weight 2^(-7(i+j)): groups d = 0, 1, 2 are
 // exact in FP32 (integers times 2^(-7d) with < 24 significant bits over a 256-wide chunk) and
@@ -54,6 +68,7 @@ struct OzArgs {
   int M, N, K;
   int k_mode;        // 0: k in [0, K); 1: k >= max(m0, n0); 2: k >= n0; 3: k >= m0
   int tiles_m, tiles_n;
+  int tiles_per_slot, tiles_total;   // set by oz_gemm
   int lower;         // only tiles with tile_m >= tile_n
   int lower_elems;   // only elements with row >= col
   float alpha, beta;
@@ -62,8 +77,9 @@ struct OzArgs {
   int32_t* err;      // device flag: set to nonzero on a timed-out wait
 };
 
-// Host: encode a 3-D tensor map over an operand's planes (box 64 x 128 x 1).
-int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes);
+// Host: encode a 3-D tensor map over an operand's planes (box OZ_KS x 128 x S: all S slices
+// of 128 rows for one pipeline stage).
+int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S);
 // Host: C = alpha C + beta A B^T for `nslots` slots (grid.z), S slices.
 int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args, int nslots, cudaStream_t st);
 
