@@ -188,7 +188,7 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(args.warmup):
+    for _ in range(max(1, args.warmup)):
         lp, st = step()
     assert np.all(st == 0), f"warm-up statuses {st.tolist()}"
     ev0 = torch.cuda.Event(enable_timing=True)

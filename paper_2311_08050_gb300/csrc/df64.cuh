@@ -52,6 +52,32 @@ static __device__ __forceinline__ df df_mul(df a, df b) {
   fast_two_sum(p, e, s, e);
   return df{s, e};
 }
+// a + b without the second error-free step on the low words: error ~2^-44 (|a| + |b|), the
+// bound of a backward-stable sum, against ~2^-44 |a + b| for df_add
+static __device__ __forceinline__ df df_add_fast(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  fast_two_sum(s, e, s, e);
+  return df{s, e};
+}
+// 1 / a: FP32 reciprocal refined by one Newton step in double-float (~2^-46 relative)
+static __device__ __forceinline__ df df_recip(df a) {
+  const float r0 = 1.0f / a.hi;
+  // residual 1 - a r0, its leading part exact through the FMA
+  const float e = __fmaf_rn(-a.lo, r0, __fmaf_rn(-a.hi, r0, 1.0f));
+  float s, t;
+  fast_two_sum(r0, r0 * e, s, t);
+  return df{s, t};
+}
+// sqrt(a), a > 0: FP32 square root refined by one Newton step in double-float
+static __device__ __forceinline__ df df_sqrt(df a) {
+  const float s0 = sqrtf(a.hi);
+  const float res = __fadd_rn(__fmaf_rn(-s0, s0, a.hi), a.lo);  // a - s0^2 (leading part exact)
+  float s, t;
+  fast_two_sum(s0, res * (0.5f / s0), s, t);
+  return df{s, t};
+}
 // a * b for an exact power-of-two scale b (no rounding unless under/overflow)
 static __device__ __forceinline__ df df_scale(df a, float p2) { return df{a.hi * p2, a.lo * p2}; }
 // acc + a * b

@@ -112,24 +112,37 @@ static void trtri64(Batch& B, int sel, int dst) {
 
 enum { V_G = 0, V_T1 = 1, V_T2 = 2, V_KV1 = 3, V_KV2 = 4 };
 
-// dst = M^-1 src for M = L L^T selected by sel; tmp receives L^-1 src
-static void solve_llt(Batch& B, int sel, int src, int tmp, int dst) {
-  const int T = sel == SEL_L ? B.max_t : B.max_tk;
-  for (int kt = 0; kt < T; ++kt) {
-    if (B.mixed) launch_trsv_fwd_df(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
-    else launch_trsv_fwd_step(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
-  }
-  for (int kt = T - 1; kt >= 0; --kt) {
-    if (B.mixed) launch_trsv_bwd_df(B.d_slots, B.n, sel, tmp, dst, kt, B.st);
-    else launch_trsv_bwd_step(B.d_slots, B.n, sel, tmp, dst, kt, T, B.st);
-  }
+static int trsv_df(Batch& B, int sel, int src, int dst, int backward) {
+  TrsvArgs a;
+  a.slots = B.d_slots;
+  a.sel = sel;
+  a.src = src;
+  a.dst = dst;
+  a.nslots = B.n;
+  a.T = sel == SEL_L ? B.max_t : B.max_tk;
+  a.backward = backward;
+  a.flags = B.flags;
+  a.err = B.err;
+  a.spin_limit = B.spin_limit;
+  return launch_trsv_df(a, B.st);
 }
-static void solve_lt(Batch& B, int sel, int src, int dst) {
+
+// dst = M^-1 src for M = L L^T selected by sel; tmp receives L^-1 src
+static int solve_llt(Batch& B, int sel, int src, int tmp, int dst) {
   const int T = sel == SEL_L ? B.max_t : B.max_tk;
-  for (int kt = T - 1; kt >= 0; --kt) {
-    if (B.mixed) launch_trsv_bwd_df(B.d_slots, B.n, sel, src, dst, kt, B.st);
-    else launch_trsv_bwd_step(B.d_slots, B.n, sel, src, dst, kt, T, B.st);
+  if (B.mixed) {
+    INLA_TRY(trsv_df(B, sel, src, tmp, 0));
+    return trsv_df(B, sel, tmp, dst, 1);
   }
+  for (int kt = 0; kt < T; ++kt) launch_trsv_fwd_step(B.d_slots, B.n, sel, src, tmp, kt, T, B.st);
+  for (int kt = T - 1; kt >= 0; --kt) launch_trsv_bwd_step(B.d_slots, B.n, sel, tmp, dst, kt, T, B.st);
+  return INLA_OK;
+}
+static int solve_lt(Batch& B, int sel, int src, int dst) {
+  const int T = sel == SEL_L ? B.max_t : B.max_tk;
+  if (B.mixed) return trsv_df(B, sel, src, dst, 1);
+  for (int kt = T - 1; kt >= 0; --kt) launch_trsv_bwd_step(B.d_slots, B.n, sel, src, dst, kt, T, B.st);
+  return INLA_OK;
 }
 
 // ---- precision-dispatched steps ----
@@ -298,16 +311,16 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
     if ((rc = debug_check(B.st, "newton assemble")) != INLA_OK) break;
     if (refactor && (rc = op_potrf(B, SEL_L)) != INLA_OK) break;
     if ((rc = debug_check(B.st, "newton potrf")) != INLA_OK) break;
-    solve_llt(B, SEL_L, V_G, V_T2, V_G);
+    if ((rc = solve_llt(B, SEL_L, V_G, V_T2, V_G)) != INLA_OK) break;
     if ((rc = debug_check(B.st, "newton solve")) != INLA_OK) break;
     launch_newton_xu(B.d_slots, NB, B.max_n, B.st);
     if (B.max_k > 0) {
       if (refactor && (rc = op_schur(B)) != INLA_OK) break;
       launch_cx(B.d_slots, NB, B.max_k, B.st);
-      solve_llt(B, SEL_S, V_KV1, V_KV2, V_KV1);
+      if ((rc = solve_llt(B, SEL_S, V_KV1, V_KV2, V_KV1)) != INLA_OK) break;
       if (B.mixed) launch_z_gemv_df(B.d_slots, NB, B.max_n, B.st);
       else launch_z_gemv(B.d_slots, NB, B.max_n, B.st);
-      solve_lt(B, SEL_L, V_T2, V_G);
+      if ((rc = solve_lt(B, SEL_L, V_T2, V_G)) != INLA_OK) break;
       launch_krige_apply(B.d_slots, NB, B.max_n, B.st);
       if ((rc = debug_check(B.st, "newton kriging")) != INLA_OK) break;
     }
@@ -475,6 +488,7 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
   B.PA = B.PB = B.PBIG = nullptr;
   B.EA = B.EB = B.EBIG = nullptr;
   B.err = cv.take<int32_t>(1);
+  B.flags = cv.take<int32_t>(G * (np / TB + 1));
   if (L.mixed) {
     const int64_t nch = (int64_t)(np + OZ_CHUNK - 1) / OZ_CHUNK;
     B.pa_cap = (int64_t)L.S * np * std::max<size_t>(256, kp);

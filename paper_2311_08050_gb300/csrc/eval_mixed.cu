@@ -1,6 +1,6 @@
 // Blocked dense routines of the mixed path.  Matrices are double-float; every product with a
 // non-trivial K runs on the Ozaki-split tensor-core GEMM; the 64 x 64 diagonal tiles are
-// factored and inverted in FP64.  Two-level blocking: 256-wide outer panels keep the
+// factored and inverted in double-float.  Two-level blocking: 256-wide outer panels keep the
 // trailing updates' K at one exact accumulation chunk (and C traffic at n^3 / (3 * 256)
 // element updates per factorisation), 64-wide inner steps keep the FP64 work small.
 #include "df64.cuh"
@@ -17,7 +17,7 @@ struct MRef {
   float2* base;       // slot-0 matrix
   int64_t stride;     // elements between slots
   int n, ld;
-  double* linv;       // slot-0 diagonal-tile inverses (n x 64 FP64)
+  double* linv;       // slot-0 diagonal-tile inverses (n x 64, double-float in FP64-sized cells)
   int64_t linv_stride;
   int sel;
 };
@@ -76,7 +76,8 @@ int mixed_potrf(Batch& B, int sel) {
       OzOperand pa = operand(B.PA, B.EA, R, IB);
       OzOperand pb = operand(B.PB, B.EB, IB, IB);
       oz_slice_df(M.base, M.stride, M.ld, j0 + IB, j0, R, IB, false, pa, S, B.n, B.st);
-      oz_slice_f64(M.linv + (int64_t)(j0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB, false, pb, S, B.n, B.st);
+      oz_slice_df(reinterpret_cast<float2*>(M.linv) + (int64_t)(j0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB,
+                  false, pb, S, B.n, B.st);
       OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(pa, pb, a, B.n, B.st));
       // rest of the 256-wide panel: A[j0+64:, j0+64:kend] -= X X_top^T
@@ -115,7 +116,8 @@ static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, i
       // X[j0 tile, 0:nc] = Linv_j X[j0 tile, 0:nc]
       OzOperand pl = operand(B.PA, B.EA, IB, IB);
       OzOperand px = operand(B.PB, B.EB, nc, IB);
-      oz_slice_f64(F.linv + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB, false, pl, S, B.n, B.st);
+      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB,
+                  false, pl, S, B.n, B.st);
       oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px, S, B.n, B.st);
       OzArgs a = gemm_args(B, X + (int64_t)j0 * ldx, x_stride, ldx, IB, nc, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(pl, px, a, B.n, B.st));

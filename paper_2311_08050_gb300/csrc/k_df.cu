@@ -150,151 +150,294 @@ __global__ void __launch_bounds__(256) k_set_identity_df(Slot* slots, int which_
   }
 }
 
-// diagonal 64-tile: load df64, Cholesky + triangular inverse in FP64 (shared memory),
-// store the factor tile in df64 (upper part zeroed) and its inverse in FP64
+// Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
+// GPU's FP64 rate is ~2 FMA/clock/SM).  Register-blocked: thread (ty, tx) of a 16 x 16 grid
+// owns the 16 elements (ty + 16 bi, tx + 16 bc); each step broadcasts one column (factor) or
+// one row and one column (inverse) through double-buffered shared arrays, one barrier per step.
+// Factor: right-looking on the unscaled columns, a_ic -= a_ij a_cj / a_jj for j < c <= i, then
+// L_ij = a_ij / sqrt(a_jj).  Inverse: right-looking on the unscaled rows of X = L^-1,
+// Y_ic -= (L_ik / L_kk) Y_kc for c <= k < i, then X_ic = Y_ic / L_ii.  Stores the factor tile
+// (double-float, upper part zeroed) and the inverse tile (double-float, in the FP64-sized
+// cells of the inverse-tile array).
 __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int kt) {
   const Slot& s = slots[blockIdx.x];
   if (!s.active) return;
   DfRef M = df_ref(s, sel);
   if (kt * TB >= M.n) return;
-  extern __shared__ double smem[];
-  double(*a)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(smem);
-  double(*inv)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(smem + TB * (TB + 1));
-  __shared__ int bad;
+  __shared__ float2 colb[2][TB], rowb[2][TB], rpb[2];
+  __shared__ float2 dsq[TB], rdq[TB];
   const int tid = threadIdx.x;
-  float2* base = M.A + (size_t)kt * TB * M.ld + (size_t)kt * TB;
-  for (int e = tid; e < TB * TB; e += blockDim.x) a[e / TB][e % TB] = df_to_double(df_load(base + (size_t)(e / TB) * M.ld + e % TB));
-  if (tid == 0) bad = 0;
-  __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
-  for (int j = 0; j < TB; ++j) {
-    if (tid == 0) {
-      double d = a[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        if (!bad) {
-          bad = 1;
-          atomicOr(&s.info[0], INFO_NOT_SPD);
-          atomicMin(&s.info[1], kt * TB + j);
+  float2* base = M.A + (size_t)kt * TB * M.ld + (size_t)kt * TB;
+  df A[4][4];
+#pragma unroll
+  for (int bi = 0; bi < 4; ++bi)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) {
+      const float2 v = base[(size_t)(ty + 16 * bi) * M.ld + tx + 16 * bc];
+      A[bi][bc] = df_make(v.x, v.y);
+    }
+  bool bad = false;
+  // ---- factor ----
+#pragma unroll
+  for (int bj = 0; bj < 4; ++bj) {
+    for (int jj = 0; jj < 16; ++jj) {
+      const int j = bj * 16 + jj, buf = j & 1;
+      if (tx == jj) {
+#pragma unroll
+        for (int bi = bj; bi < 4; ++bi) colb[buf][ty + 16 * bi] = make_float2(A[bi][bj].hi, A[bi][bj].lo);
+        if (ty == jj) {
+          df p = A[bj][bj];
+          if (!(p.hi > 0.f) || !isfinite(p.hi)) {
+            bad = true;
+            atomicMin(&s.info[1], kt * TB + j);
+            p = df_make(1.f, 0.f);
+          }
+          const df rp = df_recip(p);
+          rpb[buf] = make_float2(rp.hi, rp.lo);
         }
-        d = 1.0;
       }
-      a[j][j] = sqrt(d);
-    }
-    __syncthreads();
-    const double rdjj = 1.0 / a[j][j];
-    for (int i = j + 1 + tid; i < TB; i += blockDim.x) a[i][j] = a[i][j] * rdjj;
-    __syncthreads();
-    for (int i = j + 1 + ty; i < TB; i += 16)
-      for (int c = j + 1 + tx; c <= i; c += 16) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-    __syncthreads();
-  }
-  __shared__ double rdiag[TB];
-  if (tid < TB) rdiag[tid] = 1.0 / a[tid][tid];
-  __syncthreads();
-  if (tid < TB) {
-    const int c = tid;
-    for (int i = 0; i < c; ++i) inv[i][c] = 0.0;
-    inv[c][c] = rdiag[c];
-    for (int i = c + 1; i < TB; ++i) {
-      double acc0 = 0.0, acc1 = 0.0;
-      int k = c;
-      for (; k + 1 < i; k += 2) {
-        acc0 = fma(a[i][k], inv[k][c], acc0);
-        acc1 = fma(a[i][k + 1], inv[k + 1][c], acc1);
+      __syncthreads();
+      const df rp = df_make(rpb[buf].x, rpb[buf].y);
+#pragma unroll
+      for (int bi = bj; bi < 4; ++bi) {
+        const int i = ty + 16 * bi;
+        if (i > j) {
+          const df u = df_mul(df_make(colb[buf][i].x, colb[buf][i].y), rp);
+#pragma unroll
+          for (int bc = bj; bc <= bi; ++bc) {
+            const int c = tx + 16 * bc;
+            if (c > j && c <= i) A[bi][bc] = df_add_fast(A[bi][bc], df_neg(df_mul(u, df_make(colb[buf][c].x, colb[buf][c].y))));
+          }
+        }
       }
-      if (k < i) acc0 = fma(a[i][k], inv[k][c], acc0);
-      inv[i][c] = -(acc0 + acc1) * rdiag[i];
     }
   }
-  __syncthreads();
-  double* linv = M.Linv + (size_t)kt * TB * TB;
-  for (int e = tid; e < TB * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    df_store(base + (size_t)r * M.ld + c, c <= r ? df_from_double(a[r][c]) : df_make(0.f, 0.f));
-    linv[e] = (c <= r) ? inv[r][c] : 0.0;
+  if (bad) atomicOr(&s.info[0], INFO_NOT_SPD);
+  // ---- scaling: L_jj = sqrt(a_jj), L_ij = a_ij / L_jj ----
+  if (tx == ty) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      df p = A[b][b];
+      if (!(p.hi > 0.f) || !isfinite(p.hi)) p = df_make(1.f, 0.f);
+      const df d = df_sqrt(p), rd = df_recip(d);
+      dsq[tx + 16 * b] = make_float2(d.hi, d.lo);
+      rdq[tx + 16 * b] = make_float2(rd.hi, rd.lo);
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int bi = 0; bi < 4; ++bi)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) {
+      const int i = ty + 16 * bi, c = tx + 16 * bc;
+      if (c < i) A[bi][bc] = df_mul(A[bi][bc], df_make(rdq[c].x, rdq[c].y));
+      else if (c == i) A[bi][bc] = df_make(dsq[i].x, dsq[i].y);
+      else A[bi][bc] = df_make(0.f, 0.f);
+    }
+  // ---- inverse ----
+  df Y[4][4];
+#pragma unroll
+  for (int bi = 0; bi < 4; ++bi)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) Y[bi][bc] = df_make((ty + 16 * bi) == (tx + 16 * bc) ? 1.f : 0.f, 0.f);
+#pragma unroll
+  for (int bk = 0; bk < 4; ++bk) {
+    for (int kk = 0; kk < 16; ++kk) {
+      const int k = bk * 16 + kk, buf = k & 1;
+      if (ty == kk) {
+#pragma unroll
+        for (int bc = 0; bc <= bk; ++bc) rowb[buf][tx + 16 * bc] = make_float2(Y[bk][bc].hi, Y[bk][bc].lo);
+      }
+      if (tx == kk) {
+#pragma unroll
+        for (int bi = bk; bi < 4; ++bi) colb[buf][ty + 16 * bi] = make_float2(A[bi][bk].hi, A[bi][bk].lo);
+      }
+      __syncthreads();
+      const df rdk = df_make(rdq[k].x, rdq[k].y);
+#pragma unroll
+      for (int bi = bk; bi < 4; ++bi) {
+        const int i = ty + 16 * bi;
+        if (i > k) {
+          const df w = df_mul(df_make(colb[buf][i].x, colb[buf][i].y), rdk);
+#pragma unroll
+          for (int bc = 0; bc <= bk; ++bc) {
+            const int c = tx + 16 * bc;
+            if (c <= k) Y[bi][bc] = df_add_fast(Y[bi][bc], df_neg(df_mul(w, df_make(rowb[buf][c].x, rowb[buf][c].y))));
+          }
+        }
+      }
+    }
+  }
+  float2* linv = reinterpret_cast<float2*>(M.Linv) + (size_t)kt * TB * TB;
+#pragma unroll
+  for (int bi = 0; bi < 4; ++bi)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) {
+      const int i = ty + 16 * bi, c = tx + 16 * bc;
+      base[(size_t)i * M.ld + c] = make_float2(A[bi][bc].hi, A[bi][bc].lo);
+      const df x = c <= i ? df_mul(Y[bi][bc], df_make(rdq[i].x, rdq[i].y)) : df_make(0.f, 0.f);
+      linv[i * TB + c] = make_float2(x.hi, x.lo);
+    }
 }
 
-// vector triangular solves with a df64 factor (FP64 Linv tiles, FP64 vectors)
-__global__ void __launch_bounds__(256) k_trsv_fwd_df(Slot* slots, int sel, int src, int dst, int kt) {
-  const Slot& s = slots[blockIdx.y];
-  if (!s.active) return;
-  DfRef M = df_ref(s, sel);
-  const int T = M.n / TB, i = kt + blockIdx.x;
-  if (i >= T) return;
-  double* r = vec_ref_df(s, src);
-  double* out = vec_ref_df(s, dst);
-  __shared__ double rk[TB], y[TB];
-  __shared__ float2 yd[TB];
-  const double* linv = M.Linv + (size_t)kt * TB * TB;
-  const int tid = threadIdx.x;
-  if (tid < TB) rk[tid] = r[kt * TB + tid];
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int row = warp * 8; row < warp * 8 + 8; ++row) {
-    double v = linv[row * TB + lane] * rk[lane] + linv[row * TB + lane + 32] * rk[lane + 32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-      y[row] = v;
-      const df t = df_from_double(v);
-      yd[row] = make_float2(t.hi, t.lo);
-    }
-  }
-  __syncthreads();
-  if (i == kt) {
-    if (tid < TB) out[kt * TB + tid] = y[tid];
-    return;
-  }
-  const float2* Lik = M.A + (size_t)i * TB * M.ld + (size_t)kt * TB;
-  for (int row = warp * 8; row < warp * 8 + 8; ++row) {
-    df acc = df_mul(df_load(Lik + (size_t)row * M.ld + lane), df_make(yd[lane].x, yd[lane].y));
-    acc = df_fma(acc, df_load(Lik + (size_t)row * M.ld + lane + 32), df_make(yd[lane + 32].x, yd[lane + 32].y));
-    double v = df_to_double(acc);
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) r[i * TB + row] -= v;
-  }
+// Triangular solves with the double-float factor, one cooperative launch per solve:
+// forward dst = L^-1 src (tiles in increasing order), backward dst = L^-T src (decreasing).
+// Work items are (slot, tile) pairs in processing order, tile outermost; each block takes its
+// items in increasing order (alternating direction across blocks for balance) and, for each
+// tile its item depends on (every earlier tile of the slot), waits for that tile's ready
+// flag, then subtracts the tile's contribution.  Items only wait on earlier items, so the
+// launch makes progress when all blocks are resident (cooperative launch).  The dependency's
+// factor tile is loaded into registers before its flag is awaited.  Every wait is bounded: on
+// a timeout the block records the failure in *err and returns.  In place (src == dst) is
+// allowed: an item reads its own src tile before writing its dst tile.
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
-__global__ void __launch_bounds__(256) k_trsv_bwd_df(Slot* slots, int sel, int src, int dst, int kt) {
-  const Slot& s = slots[blockIdx.y];
-  if (!s.active) return;
-  DfRef M = df_ref(s, sel);
-  const int i = kt - (int)blockIdx.x;
-  if (kt >= M.n / TB || i < 0) return;
-  double* r = vec_ref_df(s, src);
-  double* out = vec_ref_df(s, dst);
-  __shared__ double rk[TB], y[TB];
-  __shared__ float2 yd[TB];
-  __shared__ double part[4][TB];
-  const double* linv = M.Linv + (size_t)kt * TB * TB;
-  const int tid = threadIdx.x;
-  if (tid < TB) rk[tid] = r[kt * TB + tid];
-  __syncthreads();
-  {
-    const int c = tid & 63, g = tid >> 6;
-    double v = 0.0;
-    for (int k = g * 16; k < g * 16 + 16; ++k) v = fma(linv[k * TB + c], rk[k], v);
-    part[g][c] = v;
+__device__ __forceinline__ void st_release_gpu(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ df df_shfl_xor_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df w = df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    v = df_add_fast(v, w);
   }
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_trsv_df(TrsvArgs p) {
+  __shared__ float2 vk[2][TB];
+  __shared__ float2 part[4][TB];
+  __shared__ float2 av[TB];
+  __shared__ int abort_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = tid & 63, g = tid >> 6;  // backward layout: column c, 16-row group g
+  const int P = p.T * p.nslots, G = gridDim.x;
+  if (tid == 0) abort_sh = 0;
   __syncthreads();
-  if (tid < TB) {
-    y[tid] = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
-    const df t = df_from_double(y[tid]);
-    yd[tid] = make_float2(t.hi, t.lo);
+  for (int round = 0;; ++round) {
+    const int idx = (round & 1) ? (round + 1) * G - 1 - (int)blockIdx.x : round * G + (int)blockIdx.x;
+    if (idx >= P) break;
+    const int t = idx / p.nslots, sl = idx - t * p.nslots;
+    const Slot& s = p.slots[sl];
+    if (!s.active) continue;
+    const DfRef M = df_ref(s, p.sel);
+    const int Ts = M.n / TB;
+    if (t >= Ts) continue;
+    const int i = p.backward ? Ts - 1 - t : t;
+    const double* src = vec_ref_df(s, p.src);
+    double* dst = vec_ref_df(s, p.dst);
+    int32_t* flg = p.flags + (size_t)sl * p.T;
+    const float2* Li = reinterpret_cast<const float2*>(M.Linv) + (size_t)i * TB * TB;
+    df acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = df_make(0.f, 0.f);
+    for (int u = 0; u < t; ++u) {
+      const int k = p.backward ? Ts - 1 - u : u;
+      // this dependency's factor tile: L_ik (forward, rows of tile i) or L_ki (backward)
+      float2 lv[16];
+      if (!p.backward) {
+        const float2* Lik = M.A + (size_t)i * TB * M.ld + (size_t)k * TB;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          lv[2 * r] = Lik[(size_t)(warp * 8 + r) * M.ld + lane];
+          lv[2 * r + 1] = Lik[(size_t)(warp * 8 + r) * M.ld + lane + 32];
+        }
+      } else {
+        const float2* Lki = M.A + (size_t)k * TB * M.ld + (size_t)i * TB;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) lv[r] = Lki[(size_t)(g * 16 + r) * M.ld + c];
+      }
+      if (tid == 0) {
+        bool ok = false;
+        for (int64_t it = 0; it < p.spin_limit; ++it) {
+          if (ld_acquire_gpu(flg + k) != 0) {
+            ok = true;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (!ok) {
+          abort_sh = 1;
+          atomicExch(p.err, 1);
+        }
+      }
+      __syncthreads();
+      if (abort_sh) return;
+      float2* vb = vk[u & 1];
+      if (tid < TB) {
+        const df v = df_from_double(dst[(size_t)k * TB + tid]);
+        vb[tid] = make_float2(v.hi, v.lo);
+      }
+      __syncthreads();
+      if (!p.backward) {
+        const df v0 = df_make(vb[lane].x, vb[lane].y), v1 = df_make(vb[lane + 32].x, vb[lane + 32].y);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          acc[r] = df_add_fast(acc[r], df_mul(df_make(lv[2 * r].x, lv[2 * r].y), v0));
+          acc[r] = df_add_fast(acc[r], df_mul(df_make(lv[2 * r + 1].x, lv[2 * r + 1].y), v1));
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          acc[r & 7] = df_add_fast(acc[r & 7], df_mul(df_make(lv[r].x, lv[r].y), df_make(vb[g * 16 + r].x, vb[g * 16 + r].y)));
+      }
+    }
+    // a = src_i - (sum of the dependencies)
+    if (!p.backward) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const df v = df_shfl_xor_sum(acc[r]);
+        if (lane == 0) part[0][warp * 8 + r] = make_float2(v.hi, v.lo);
+      }
+    } else {
+      df v = acc[0];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v = df_add_fast(v, acc[r]);
+      part[g][c] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    if (tid < TB) {
+      df sum = df_make(part[0][tid].x, part[0][tid].y);
+      if (p.backward)
+        for (int q = 1; q < 4; ++q) sum = df_add_fast(sum, df_make(part[q][tid].x, part[q][tid].y));
+      const df a = df_add_fast(df_from_double(src[(size_t)i * TB + tid]), df_neg(sum));
+      av[tid] = make_float2(a.hi, a.lo);
+    }
+    __syncthreads();
+    // diagonal tile: dst_i = Linv_i a (forward) or Linv_i^T a (backward)
+    if (!p.backward) {
+      const df a0 = df_make(av[lane].x, av[lane].y), a1 = df_make(av[lane + 32].x, av[lane + 32].y);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = warp * 8 + r;
+        df v = df_mul(df_make(Li[row * TB + lane].x, Li[row * TB + lane].y), a0);
+        v = df_add_fast(v, df_mul(df_make(Li[row * TB + lane + 32].x, Li[row * TB + lane + 32].y), a1));
+        v = df_shfl_xor_sum(v);
+        if (lane == 0) dst[(size_t)i * TB + row] = df_to_double(v);
+      }
+    } else {
+      df v = df_make(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const float2 l = Li[(g * 16 + r) * TB + c];
+        v = df_add_fast(v, df_mul(df_make(l.x, l.y), df_make(av[g * 16 + r].x, av[g * 16 + r].y)));
+      }
+      part[g][c] = make_float2(v.hi, v.lo);
+      __syncthreads();
+      if (tid < TB) {
+        df sum = df_make(part[0][tid].x, part[0][tid].y);
+        for (int q = 1; q < 4; ++q) sum = df_add_fast(sum, df_make(part[q][tid].x, part[q][tid].y));
+        dst[(size_t)i * TB + tid] = df_to_double(sum);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release_gpu(flg + i, 1);
   }
-  __syncthreads();
-  if (i == kt) {
-    if (tid < TB) out[kt * TB + tid] = y[tid];
-    return;
-  }
-  const float2* Lki = M.A + (size_t)kt * TB * M.ld + (size_t)i * TB;
-  {
-    const int c = tid & 63, g = tid >> 6;
-    df acc = df_make(0.f, 0.f);
-    for (int k = g * 16; k < g * 16 + 16; ++k) acc = df_fma(acc, df_load(Lki + (size_t)k * M.ld + c), df_make(yd[k].x, yd[k].y));
-    part[g][c] = df_to_double(acc);
-  }
-  __syncthreads();
-  if (tid < TB) r[i * TB + tid] -= ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
 }
 
 __global__ void __launch_bounds__(256) k_logdet_df(Slot* slots, int sel, int out_idx) {
@@ -378,19 +521,27 @@ void launch_set_identity_df(Slot* slots, int nslots, int which_wk, int size_sel,
   count_launch("k_set_identity_df"), k_set_identity_df<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots, which_wk, size_sel);
 }
 void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st) {
-  static bool init = false;
-  const int smem = 2 * TB * (TB + 1) * (int)sizeof(double);
-  if (!init) {
-    cudaFuncSetAttribute(k_potrf_diag_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    init = true;
+  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, 0, st>>>(slots, sel, kt);
+}
+int launch_trsv_df(const TrsvArgs& a, cudaStream_t st) {
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_df, 256, 0) != cudaSuccess || per_sm <= 0)
+      return INLA_E_CUDA;
   }
-  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, smem, st>>>(slots, sel, kt);
-}
-void launch_trsv_fwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t, cudaStream_t st) {
-  count_launch("k_trsv_fwd_df"), k_trsv_fwd_df<<<dim3(max_t - kt, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
-}
-void launch_trsv_bwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, cudaStream_t st) {
-  count_launch("k_trsv_bwd_df"), k_trsv_bwd_df<<<dim3(kt + 1, nslots), 256, 0, st>>>(slots, sel, src, dst, kt);
+  const int items = a.T * a.nslots;
+  if (items <= 0) return INLA_OK;
+  if (cudaMemsetAsync(a.flags, 0, sizeof(int32_t) * (size_t)items, st) != cudaSuccess) return INLA_E_CUDA;
+  const int grid = std::min(items, per_sm * sms);
+  TrsvArgs args = a;
+  void* params[] = {&args};
+  count_launch("k_trsv_df");
+  if (cudaLaunchCooperativeKernel((const void*)k_trsv_df, dim3(grid), dim3(256), params, 0, st) != cudaSuccess)
+    return note_launch_error("k_trsv_df cooperative launch");
+  return INLA_OK;
 }
 void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st) {
   count_launch("k_logdet_df"), k_logdet_df<<<nslots, 256, 0, st>>>(slots, sel, out_idx);

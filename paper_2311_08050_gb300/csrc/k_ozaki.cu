@@ -421,33 +421,38 @@ __device__ __forceinline__ df load_df<double>(const double* p) {
   return df_from_double(*p);
 }
 
-// slice the 8 values of one lane (already loaded) given the warp-wide exponent; write S planes
+// Slice the 8 values of one lane, given the exponent e of their (row, chunk): x 2^(7-e) has
+// magnitude <= 128; slice s is v_s = round(h) of the running remainder h (scaled by 2^7 per
+// slice), stored as the BF16 number v_s 2^(-7s) -- exact: |v_s| <= 128 has at most 8
+// significant bits, so the BF16 encoding is the upper half of the FP32 one.  The remainder
+// h - v_s is exact (Sterbenz), and adding the low word back is exact too: h - v_s is zero or a
+// multiple of ulp(h), at least twice the low word.  Integer rounding by the 1.5 * 2^23 shift.
 __device__ __forceinline__ void slice_and_store(const df (&x)[8], int e, uint16_t* planes, int64_t plane_stride,
                                                 int S, int64_t base, bool valid) {
-  const float sc = pow2f(7 - e);  // t * 2^7 with t = x 2^-e, |t| <= 1
-  df r[8];
+  constexpr float kRound = 12582912.f;  // 1.5 * 2^23
+  const float sc = pow2f(7 - e);
+  float h[8], l[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) r[i] = df_scale(x[i], sc);
+  for (int i = 0; i < 8; ++i) {
+    h[i] = x[i].hi * sc;
+    l[i] = x[i].lo * sc;
+  }
+  float p7 = 1.f;  // 2^(-7s)
   for (int s = 0; s < S; ++s) {
-    uint16_t out[8];
+    uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float v = rintf(r[i].hi + r[i].lo);
-      // remainder (exact): (hi - v) + lo, then scaled by 2^7 for the next slice
-      df rem = df_add_f(df_make(r[i].hi - v, 0.f), r[i].lo);
-      r[i] = df_scale(rem, 128.f);
-      // slice s is stored as v_s 2^(-7s) (exact: a power-of-two scaling of an integer <= 2^8)
-      const __nv_bfloat16 bv = __float2bfloat16_rn(v * pow2f(-7 * s));
-      out[i] = *reinterpret_cast<const uint16_t*>(&bv);
+      const float v = __fsub_rn(__fadd_rn(h[i], kRound), kRound);
+      const uint32_t bits = __float_as_uint(v * p7) >> 16;
+      if (i & 1) w[i >> 1] |= bits << 16;
+      else w[i >> 1] = bits;
+      float a, b;
+      fast_two_sum(__fsub_rn(h[i], v), l[i], a, b);
+      h[i] = a * 128.f;
+      l[i] = b * 128.f;
     }
-    if (valid) {
-      uint4 pk;
-      pk.x = (uint32_t)out[0] | ((uint32_t)out[1] << 16);
-      pk.y = (uint32_t)out[2] | ((uint32_t)out[3] << 16);
-      pk.z = (uint32_t)out[4] | ((uint32_t)out[5] << 16);
-      pk.w = (uint32_t)out[6] | ((uint32_t)out[7] << 16);
-      *reinterpret_cast<uint4*>(planes + s * plane_stride + base) = pk;
-    }
+    if (valid) *reinterpret_cast<uint4*>(planes + s * plane_stride + base) = make_uint4(w[0], w[1], w[2], w[3]);
+    p7 *= 0.0078125f;
   }
 }
 
@@ -460,18 +465,20 @@ __device__ __forceinline__ int chunk_exponent(float m) {
   return e;
 }
 
-// untransposed source: one warp per (operand row, chunk); lane covers k = lane*8 .. +7
-template <typename T>
+// Untransposed source: a group of G lanes (8, 16 or 32: the chunk width / 8) per (operand
+// row, chunk); lane g of the group covers k = chunk * 256 + 8g .. +7.
+template <typename T, int G>
 __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
                                                     int R, int K, OzOperand dst, int S) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int nchunks = (K + OZ_CHUNK - 1) / OZ_CHUNK;
-  if (warp >= R * nchunks) return;
-  const int r = warp / nchunks, ch = warp % nchunks;
+  const bool active = grp < (int64_t)R * nchunks;
+  const int r = active ? (int)(grp / nchunks) : 0, ch = active ? (int)(grp % nchunks) : 0;
   const int slot = blockIdx.y;
   const T* s = src + slot * src_slot_stride + (int64_t)(row0 + r) * ld + col0;
-  const int k0 = ch * OZ_CHUNK + lane * 8;
-  const bool valid = k0 < K;
+  const int k0 = ch * OZ_CHUNK + gl * 8;
+  const bool valid = active && k0 < K;
   df x[8];
   float mx = 0.f;
 #pragma unroll
@@ -480,19 +487,23 @@ __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_sl
     mx = fmaxf(mx, fabsf(x[i].hi));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = G / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   // |x| <= |hi| (1 + 2^-24): round the bound up so that |x| 2^-e <= 1 holds
   const int e = chunk_exponent(mx * (1.0f + 1.2e-7f));
-  if (lane == 0) dst.exps[slot * dst.exp_slot_stride + (int64_t)ch * dst.exp_chunk_stride + r] = e;
+  if (active && gl == 0) dst.exps[slot * dst.exp_slot_stride + (int64_t)ch * dst.exp_chunk_stride + r] = e;
   uint16_t* planes = dst.planes + (int64_t)slot * S * dst.plane_stride;
   slice_and_store(x, e, planes, dst.plane_stride, S, (int64_t)r * dst.ld_k + k0, valid);
 }
 
-// transposed source: a block handles 16 operand rows x one 256-chunk through shared memory
+// Transposed source: a block handles 16 operand rows x one 256-chunk through shared memory.
+// The tile is stored row-major by operand row with the k index swizzled (k ^ ((k >> 3) & 15)),
+// so that both the transposing writes (16 rows, one k) and the per-lane reads (one row, k =
+// 8 lane + i) are free of bank conflicts.
 template <typename T>
 __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
                                                     int R, int K, OzOperand dst, int S) {
-  __shared__ float2 tile[OZ_CHUNK][17];
+  constexpr int LDT = OZ_CHUNK + 1;  // odd row stride (float2): the 16 rows of a write hit distinct banks
+  __shared__ float2 tile[16 * LDT];
   const int r0 = blockIdx.x * 16, ch = blockIdx.z, slot = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* s = src + slot * src_slot_stride;
@@ -500,7 +511,7 @@ __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_sl
     const int k = ch * OZ_CHUNK + kk, r = r0 + (lane & 15);
     df v = df_make(0.f, 0.f);
     if (k < K && r < R) v = load_df<T>(s + (int64_t)(row0 + k) * ld + col0 + r);
-    tile[kk][lane & 15] = make_float2(v.hi, v.lo);
+    tile[(lane & 15) * LDT + (kk ^ ((kk >> 3) & 15))] = make_float2(v.hi, v.lo);
   }
   __syncthreads();
   for (int rr = warp * 2; rr < warp * 2 + 2; ++rr) {
@@ -512,7 +523,8 @@ __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_sl
     float mx = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float2 t = tile[lane * 8 + i][rr];
+      const int kk = lane * 8 + i;
+      const float2 t = tile[rr * LDT + (kk ^ ((kk >> 3) & 15))];
       x[i] = df_make(t.x, t.y);
       mx = fmaxf(mx, fabsf(t.x));
     }
@@ -705,8 +717,14 @@ static void slice_impl(const T* src, int64_t sss, int ld, int row0, int col0, in
   if (R <= 0 || K <= 0) return;
   const int nchunks = (K + OZ_CHUNK - 1) / OZ_CHUNK;
   if (!transposed) {
-    const int64_t warps = (int64_t)R * nchunks;
-    count_launch("k_slice_rows<T>"), k_slice_rows<T><<<dim3((unsigned)((warps + 7) / 8), nslots), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    // lanes per (row, chunk): the chunk width / 8 (K is a multiple of 64)
+    const int G = K >= OZ_CHUNK ? 32 : K <= 64 ? 8 : K <= 128 ? 16 : 32;
+    const int64_t threads = (int64_t)R * nchunks * G;
+    const dim3 grid((unsigned)((threads + 255) / 256), nslots);
+    count_launch("k_slice_rows<T>");
+    if (G == 8) k_slice_rows<T, 8><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    else if (G == 16) k_slice_rows<T, 16><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    else k_slice_rows<T, 32><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   } else {
     count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   }

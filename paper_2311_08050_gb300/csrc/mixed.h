@@ -1,5 +1,5 @@
-// Mixed-precision path: double-float matrices, Ozaki-split tensor-core GEMMs, FP64 64 x 64
-// diagonal tiles.  Declarations shared by eval.cu, eval_mixed.cu and k_df.cu.
+// Mixed-precision path: double-float matrices, Ozaki-split tensor-core GEMMs, double-float
+// 64 x 64 diagonal tiles.  Declarations shared by eval.cu, eval_mixed.cu and k_df.cu.
 #pragma once
 #include "kernels.h"
 #include "ozaki.h"
@@ -16,8 +16,17 @@ void launch_z_gemv_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
 void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st);
 void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st);
 void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st);
-void launch_trsv_fwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, int max_t, cudaStream_t st);
-void launch_trsv_bwd_df(Slot* slots, int nslots, int sel, int src, int dst, int kt, cudaStream_t st);
+// triangular solve with a double-float factor (one cooperative launch; see k_df.cu)
+struct TrsvArgs {
+  Slot* slots;
+  int sel, src, dst;
+  int nslots, T;        // slots, tile rows of the largest factor
+  int backward;         // 0: dst = L^-1 src; 1: dst = L^-T src
+  int32_t* flags;       // nslots x T ready flags (zeroed by the launcher)
+  int32_t* err;         // set on a timed-out wait
+  int64_t spin_limit;
+};
+int launch_trsv_df(const TrsvArgs& a, cudaStream_t st);
 void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st);
 void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
@@ -44,6 +53,7 @@ struct Batch {
   int64_t pa_cap, pb_cap, pbig_cap;   // elements per slot
   int64_t ea_cap, eb_cap, ebig_cap;   // exponents per slot
   int32_t* err;
+  int32_t* flags;        // ready flags of the cooperative triangular solves (slots x tiles)
   int64_t spin_limit;
 };
 
