@@ -205,12 +205,8 @@ def run_ours(args):
     timed_launches = int(L.inla_test_launch_count())
     ms = ev0.elapsed_time(ev1)
     t_local = ms / 1e3
-    t_max = t_local
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_local], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    from paper_2311_08050_gb300 import replicas
+    t_max = replicas.max_over_ranks(t_local, world)
     value = world * nb * args.steps / t_max
     # ---------------- roofline of the dominant kernel (instrumented extra step) ----------------
     L.inla_test_stats_enable(1)
