@@ -1,5 +1,5 @@
-"""The C-ABI library builds, loads, and exports every entry point include/inla.h declares
-(CPU only: no compute call needs a GPU here)."""
+"""The C-ABI library builds, loads, and exports every entry point the headers in include/
+declare (CPU only: no compute call needs a GPU here)."""
 import ctypes
 import os
 import re
@@ -13,10 +13,14 @@ from paper_2311_08050_gb300 import inla
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    txt = open(os.path.join(ROOT, "include", "inla.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(inla_[a-z0-9_]+)\s*\(", txt)))
+def _declared(header=None):
+    names = [header] if header else sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    found = set()
+    for h in names:
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        found |= set(re.findall(r"\b(inla_[a-z0-9_]+)\s*\(", txt))
+    return sorted(found)
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +29,20 @@ def libpath():
 
 
 def test_header_declares_the_binding_entry_points():
-    assert set(inla.EXPORTED) <= set(_declared())
+    assert set(inla.EXPORTED) <= set(_declared("inla.h"))
+    assert {"inla_mlp_create", "inla_mlp_train", "inla_mlp_predict", "inla_mlp_loss_grad"} <= set(
+        _declared("inla_surrogate.h"))
+
+
+def test_surrogate_parameter_count_and_argument_checks_without_a_gpu(libpath):
+    from oracle import mlp_oracle
+    L = inla.lib()
+    L.inla_mlp_num_params.restype = ctypes.c_int64
+    for d in (1, 4, 8):
+        assert L.inla_mlp_num_params(d) == mlp_oracle.n_params(d, 128)
+    h = ctypes.c_void_p()
+    assert L.inla_mlp_create(0, 16, ctypes.byref(h)) == inla.E_BADARG
+    assert L.inla_mlp_create(9, 16, ctypes.byref(h)) == inla.E_BADARG
 
 
 def test_library_exports_every_declared_symbol(libpath):
