@@ -241,7 +241,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": f"bf16 Ozaki slices x{args.slices} (prior, final factor) / x{args.newton_slices} (Newton), "
-                    "exact fp32 accumulation + df64 storage + f64 diagonal tiles"
+                    "exact fp32 accumulation + df64 storage and diagonal tiles"
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
            "config": {"workload": WORKLOADS[args.config], "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
