@@ -71,21 +71,13 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 template <int S>
 struct OzCfg {
   static constexpr int STAGE_BYTES = 2 * S * OZ_SLICE_BYTES;
-  static constexpr int NST_FIT = (OZ_SMEM_BUDGET - 1024 - OZ_STAGING_BYTES) / STAGE_BYTES;
+  static constexpr int NST_FIT = (OZ_SMEM_BUDGET - 1024 - OZ_STAGING_BYTES - OZ_COLSC_BYTES) / STAGE_BYTES;
   static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
-  static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OZ_STAGING_BYTES;  // 1024: alignment slack
+  static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OZ_STAGING_BYTES + OZ_COLSC_BYTES;  // 1024: alignment
   static constexpr int NACC = S < OZ_NACC ? S : OZ_NACC;
   static constexpr uint32_t TMEM_COLS = NACC * OZ_BN <= 256 ? 256 : 512;
 };
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) |
@@ -99,6 +91,86 @@ __device__ __forceinline__ float2 df2_add_fast(float2 a, float2 b) {
   t = __fadd_rn(t, __fadd_rn(a.y, b.y));
   fast_two_sum(s, t, s, t);
   return make_float2(s, t);
+}
+// Packed FP32 pairs (f32x2: two lanes of arithmetic per instruction on the FP32 pipe).
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(uint64_t v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Load 8 consecutive TMEM columns of NA accumulators (columns col + a * OZ_BN), wait for the
+// loads, and return them as packed column pairs d[a][m] = (column 2m, column 2m + 1).  One asm
+// statement: the registers are read only after tcgen05.wait::ld.
+template <int NA>
+__device__ __forceinline__ void tmem_ld8_pairs(uint32_t taddr, uint64_t (&d)[NA][4]);
+template <>
+__device__ __forceinline__ void tmem_ld8_pairs<2>(uint32_t t, uint64_t (&d)[2][4]) {
+  asm volatile(
+      "{\n.reg .b32 a<16>;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%8];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%9];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
+      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
+        "=l"(d[1][3])
+      : "r"(t), "r"(t + OZ_BN)
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld8_pairs<3>(uint32_t t, uint64_t (&d)[3][4]) {
+  asm volatile(
+      "{\n.reg .b32 a<24>;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%12];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%13];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a16,a17,a18,a19,a20,a21,a22,a23}, [%14];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
+      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n"
+      "mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
+        "=l"(d[1][3]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3])
+      : "r"(t), "r"(t + OZ_BN), "r"(t + 2 * OZ_BN)
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld8_pairs<4>(uint32_t t, uint64_t (&d)[4][4]) {
+  asm volatile(
+      "{\n.reg .b32 a<32>;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a16,a17,a18,a19,a20,a21,a22,a23}, [%18];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a24,a25,a26,a27,a28,a29,a30,a31}, [%19];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
+      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n"
+      "mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23};\n"
+      "mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
+        "=l"(d[1][3]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[3][0]), "=l"(d[3][1]),
+        "=l"(d[3][2]), "=l"(d[3][3])
+      : "r"(t), "r"(t + OZ_BN), "r"(t + 2 * OZ_BN), "r"(t + 3 * OZ_BN)
+      : "memory");
 }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Tile t of the launch (slots outermost): its slot, origin and K range in 32-wide stages.
@@ -143,6 +215,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float2* staging = reinterpret_cast<float2*>(smem + NST * STAGE_BYTES);
+  float* colsc_all = reinterpret_cast<float*>(smem + NST * STAGE_BYTES + OZ_STAGING_BYTES);
   __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full, acc_empty, done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh_;
@@ -271,6 +344,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int q = warp & 3, h = ew >> 2;
     const int row = q * 32 + lane;
     float2* stg = staging + ew * (32 * OZ_STG_LD);
+    float* colsc = colsc_all + ew * 64;
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
     const bool neg = p.beta < 0.f;
     const bool accumulate = p.alpha != 0.f;
@@ -282,7 +356,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int gr = ti.m0 + row;
       const int col0 = ti.n0 + h * 64;
       float2* C = p.C + ti.slot * p.C_slot_stride;
-      float2 acc[64];
+      float2 acc[64];  // the register tile: (hi, lo) of the thread's 64 columns
       if (ti.n_st == 0) {
         if (p.alpha != 0.f) continue;
 #pragma unroll
@@ -296,13 +370,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int k = ti.k_lo; k < p.K;) {
           const int chunk = k / OZ_CHUNK;
           const int k_end = min(p.K, (chunk + 1) * OZ_CHUNK);
-          // scales of this chunk: +-2^(eA - 14) for the thread's row (sign of beta); 2^eB for
-          // columns lane and lane + 32, shuffled to the other lanes
+          // scales of this chunk: +-2^(eA - 14) for the thread's row (sign of beta); 2^eB for the
+          // warp's 64 columns in a per-warp shared array (read as broadcast pairs)
           float rs = pow2f(gr < p.M ? eA[(int64_t)chunk * p.expA_chunk_stride + gr] - 14 : 0);
           if (neg) rs = -rs;
+          const uint64_t rs2 = f2pack(rs, rs);
           const int64_t eb_base = (int64_t)chunk * p.expB_chunk_stride;
-          const float cs0 = pow2f(col0 + lane < p.N ? eB[eb_base + col0 + lane] : 0);
-          const float cs1 = pow2f(col0 + 32 + lane < p.N ? eB[eb_base + col0 + 32 + lane] : 0);
+          __syncwarp();
+          colsc[lane] = pow2f(col0 + lane < p.N ? eB[eb_base + col0 + lane] : 0);
+          colsc[lane + 32] = pow2f(col0 + 32 + lane < p.N ? eB[eb_base + col0 + 32 + lane] : 0);
+          __syncwarp();
           bool got = mbar_wait(&acc_full, c & 1, lim);
           got = __all_sync(0xffffffffu, got);
           if (!got) {
@@ -313,39 +390,37 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const bool first = (k == ti.k_lo);
 #pragma unroll
           for (int blk = 0; blk < 8; ++blk) {
-            float D[NACC][8];
+            uint64_t D[NACC][4];
+            tmem_ld8_pairs<NACC>(t_lane + (uint32_t)(h * 64 + blk * 8), D);
+            // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14 below
+            // 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the fractions
+            // exactly into the low word (multiples of 2^-14 below 1), and the rounded tail group
+            // (d >= 3) costs ~2^-24 of a value below 2^4.  Integer parts by the 1.5 * 2^23 shift
+            // (exact for |x| < 2^22); two columns per f32x2 instruction.
+            const uint64_t KR2 = f2pack(kRound, kRound);
 #pragma unroll
-            for (int d = 0; d < NACC; ++d) tmem_ld8(t_lane + (uint32_t)(d * OZ_BN + h * 64 + blk * 8), D[d]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int d = 0; d < NACC; ++d)
-#pragma unroll
-              for (int cc = 0; cc < 8; ++cc) asm volatile("" : "+f"(D[d][cc]));
-#pragma unroll
-            for (int cc = 0; cc < 8; ++cc) {
-              const int j = blk * 8 + cc;
-              // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14
-              // below 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the
-              // fractions exactly into the low word (multiples of 2^-14 below 1), and the
-              // rounded tail group (d >= 3) costs ~2^-24 of a value below 2^4.
-              // (Integer parts by the 1.5 * 2^23 shift, exact for |x| < 2^22, on the FP32 pipe.)
-              float s = D[0][cc], e = 0.f;
-              {
-                const float t = __fsub_rn(__fadd_rn(D[1][cc], kRound), kRound);
-                s = __fadd_rn(s, t);
-                e = __fsub_rn(D[1][cc], t);
-              }
+            for (int m = 0; m < 4; ++m) {
+              const int j2 = blk * 4 + m;  // column pair (2 j2, 2 j2 + 1) of the thread's 64
+              const uint64_t d1 = D[1][m];
+              const uint64_t t1 = sub2(add2(d1, KR2), KR2);
+              uint64_t sv = add2(D[0][m], t1);
+              uint64_t ev = sub2(d1, t1);
               if (NACC >= 3) {
-                const float t = __fsub_rn(__fadd_rn(D[2][cc], kRound), kRound);
-                s = __fadd_rn(s, t);
-                e = __fadd_rn(e, __fsub_rn(D[2][cc], t));
+                const uint64_t d2 = D[2][m];
+                const uint64_t t2 = sub2(add2(d2, KR2), KR2);
+                sv = add2(sv, t2);
+                ev = add2(ev, sub2(d2, t2));
               }
-              if (NACC >= 4) e = __fadd_rn(e, D[NACC - 1][cc]);
-              const float sc = rs * __shfl_sync(0xffffffffu, j < 32 ? cs0 : cs1, j & 31);
+              if (NACC >= 4) ev = add2(ev, D[NACC - 1][m]);
+              const uint64_t sc = mul2(rs2, *reinterpret_cast<const uint64_t*>(colsc + 2 * j2));
+              const uint64_t hi = mul2(sv, sc), lo = mul2(ev, sc);
+              const float2 hh = f2unpack(hi), ll = f2unpack(lo);
               if (first) {
-                acc[j] = make_float2(s * sc, e * sc);
+                acc[2 * j2] = make_float2(hh.x, ll.x);
+                acc[2 * j2 + 1] = make_float2(hh.y, ll.y);
               } else {
-                acc[j] = df2_add_fast(acc[j], make_float2(s * sc, e * sc));
+                acc[2 * j2] = df2_add_fast(acc[2 * j2], make_float2(hh.x, ll.x));
+                acc[2 * j2 + 1] = df2_add_fast(acc[2 * j2 + 1], make_float2(hh.y, ll.y));
               }
             }
           }
@@ -356,7 +431,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
         if (!ok) break;
       }
-      // C update through the staging buffer, 8 columns at a time: 8 lanes per row segment
       const int cc = lane & 7;
       int grow[8];
       float2* crow[8];

@@ -33,6 +33,7 @@ constexpr int OZ_EPI_REGS = 224;
 static_assert(4 * OZ_ROLE_REGS + 8 * OZ_EPI_REGS <= 12 * 168, "register split exceeds the launch allocation");
 constexpr int OZ_STG_LD = 9;                        // epilogue staging row stride (float2)
 constexpr int OZ_STAGING_BYTES = OZ_EPI_WARPS * 32 * OZ_STG_LD * 8;
+constexpr int OZ_COLSC_BYTES = OZ_EPI_WARPS * 64 * 4;  // per-warp column scale factors
 constexpr int OZ_SMEM_BUDGET = 232448 - 512;        // opt-in maximum less the static barriers
 // TMEM accumulators per tile (4 x 128 columns = all 512).  Slice i is stored pre-scaled by
 // 2^(-7i), so a product V_i W_j^T arrives with its weight 2^(-7(i+j)): groups d = 0, 1, 2 are
