@@ -48,9 +48,11 @@ __global__ void __launch_bounds__(H) k_mlp_fwd(const float* __restrict__ P, cons
     const int r = e / H, c = e % H;  // W2[r][c]
     W2T[c * H + r] = P[o.W2 + e];
   }
-  for (int e = i; e < TS * D; e += H) {
-    const int s = e / D, d = e % D;
-    xs[s * INLA_MLP_MAX_DIN + d] = s0 + s < N ? X[(size_t)(s0 + s) * D + d] : 0.f;
+  // every slot of the input tile is written (zeros beyond D and N): the unrolled layer-1 loop
+  // reads all INLA_MLP_MAX_DIN of them
+  for (int e = i; e < TS * INLA_MLP_MAX_DIN; e += H) {
+    const int s = e / INLA_MLP_MAX_DIN, d = e % INLA_MLP_MAX_DIN;
+    xs[e] = (s0 + s < N && d < D) ? X[(size_t)(s0 + s) * D + d] : 0.f;
   }
   __syncthreads();
   float w1[INLA_MLP_MAX_DIN];

@@ -118,58 +118,48 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
-// Load 8 consecutive TMEM columns of NA accumulators (columns col + a * OZ_BN), wait for the
+// Load 16 consecutive TMEM columns of NA accumulators (columns col + a * OZ_BN), wait for the
 // loads, and return them as packed column pairs d[a][m] = (column 2m, column 2m + 1).  One asm
 // statement: the registers are read only after tcgen05.wait::ld.
 template <int NA>
-__device__ __forceinline__ void tmem_ld8_pairs(uint32_t taddr, uint64_t (&d)[NA][4]);
+__device__ __forceinline__ void tmem_ld16_pairs(uint32_t taddr, uint64_t (&d)[NA][8]);
 template <>
-__device__ __forceinline__ void tmem_ld8_pairs<2>(uint32_t t, uint64_t (&d)[2][4]) {
-  asm volatile(
-      "{\n.reg .b32 a<16>;\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%8];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%9];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
-      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n}"
-      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
-        "=l"(d[1][3])
-      : "r"(t), "r"(t + OZ_BN)
-      : "memory");
-}
-template <>
-__device__ __forceinline__ void tmem_ld8_pairs<3>(uint32_t t, uint64_t (&d)[3][4]) {
-  asm volatile(
-      "{\n.reg .b32 a<24>;\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%12];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%13];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a16,a17,a18,a19,a20,a21,a22,a23}, [%14];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
-      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n"
-      "mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23};\n}"
-      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
-        "=l"(d[1][3]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3])
-      : "r"(t), "r"(t + OZ_BN), "r"(t + 2 * OZ_BN)
-      : "memory");
-}
-template <>
-__device__ __forceinline__ void tmem_ld8_pairs<4>(uint32_t t, uint64_t (&d)[4][4]) {
+__device__ __forceinline__ void tmem_ld16_pairs<2>(uint32_t t, uint64_t (&d)[2][8]) {
   asm volatile(
       "{\n.reg .b32 a<32>;\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a0,a1,a2,a3,a4,a5,a6,a7}, [%16];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a8,a9,a10,a11,a12,a13,a14,a15}, [%17];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a16,a17,a18,a19,a20,a21,a22,a23}, [%18];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {a24,a25,a26,a27,a28,a29,a30,a31}, [%19];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a16,a17,a18,a19,a20,a21,a22,a23,a24,a25,a26,a27,a28,a29,a30,a31}, [%17];\n"
       "tcgen05.wait::ld.sync.aligned;\n"
-      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7};\n"
-      "mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15};\n"
-      "mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23};\n"
-      "mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31};\n}"
-      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]),
-        "=l"(d[1][3]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[3][0]), "=l"(d[3][1]),
-        "=l"(d[3][2]), "=l"(d[3][3])
-      : "r"(t), "r"(t + OZ_BN), "r"(t + 2 * OZ_BN), "r"(t + 3 * OZ_BN)
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7])
+      : "r"(t), "r"(t + 1 * OZ_BN)
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld16_pairs<3>(uint32_t t, uint64_t (&d)[3][8]) {
+  asm volatile(
+      "{\n.reg .b32 a<48>;\n"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a16,a17,a18,a19,a20,a21,a22,a23,a24,a25,a26,a27,a28,a29,a30,a31}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a32,a33,a34,a35,a36,a37,a38,a39,a40,a41,a42,a43,a44,a45,a46,a47}, [%26];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31}; mov.b64 %16, {a32,a33}; mov.b64 %17, {a34,a35}; mov.b64 %18, {a36,a37}; mov.b64 %19, {a38,a39}; mov.b64 %20, {a40,a41}; mov.b64 %21, {a42,a43}; mov.b64 %22, {a44,a45}; mov.b64 %23, {a46,a47};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[2][4]), "=l"(d[2][5]), "=l"(d[2][6]), "=l"(d[2][7])
+      : "r"(t), "r"(t + 1 * OZ_BN), "r"(t + 2 * OZ_BN)
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld16_pairs<4>(uint32_t t, uint64_t (&d)[4][8]) {
+  asm volatile(
+      "{\n.reg .b32 a<64>;\n"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a16,a17,a18,a19,a20,a21,a22,a23,a24,a25,a26,a27,a28,a29,a30,a31}, [%33];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a32,a33,a34,a35,a36,a37,a38,a39,a40,a41,a42,a43,a44,a45,a46,a47}, [%34];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a48,a49,a50,a51,a52,a53,a54,a55,a56,a57,a58,a59,a60,a61,a62,a63}, [%35];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31}; mov.b64 %16, {a32,a33}; mov.b64 %17, {a34,a35}; mov.b64 %18, {a36,a37}; mov.b64 %19, {a38,a39}; mov.b64 %20, {a40,a41}; mov.b64 %21, {a42,a43}; mov.b64 %22, {a44,a45}; mov.b64 %23, {a46,a47}; mov.b64 %24, {a48,a49}; mov.b64 %25, {a50,a51}; mov.b64 %26, {a52,a53}; mov.b64 %27, {a54,a55}; mov.b64 %28, {a56,a57}; mov.b64 %29, {a58,a59}; mov.b64 %30, {a60,a61}; mov.b64 %31, {a62,a63};\n}"
+      : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[2][4]), "=l"(d[2][5]), "=l"(d[2][6]), "=l"(d[2][7]), "=l"(d[3][0]), "=l"(d[3][1]), "=l"(d[3][2]), "=l"(d[3][3]), "=l"(d[3][4]), "=l"(d[3][5]), "=l"(d[3][6]), "=l"(d[3][7])
+      : "r"(t), "r"(t + 1 * OZ_BN), "r"(t + 2 * OZ_BN), "r"(t + 3 * OZ_BN)
       : "memory");
 }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -389,9 +379,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;");
           const bool first = (k == ti.k_lo);
 #pragma unroll
-          for (int blk = 0; blk < 8; ++blk) {
-            uint64_t D[NACC][4];
-            tmem_ld8_pairs<NACC>(t_lane + (uint32_t)(h * 64 + blk * 8), D);
+          for (int blk2 = 0; blk2 < 4; ++blk2) {
+            uint64_t D[NACC][8];
+            tmem_ld16_pairs<NACC>(t_lane + (uint32_t)(h * 64 + blk2 * 16), D);
             // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14 below
             // 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the fractions
             // exactly into the low word (multiples of 2^-14 below 1), and the rounded tail group
@@ -399,8 +389,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // (exact for |x| < 2^22); two columns per f32x2 instruction.
             const uint64_t KR2 = f2pack(kRound, kRound);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int j2 = blk * 4 + m;  // column pair (2 j2, 2 j2 + 1) of the thread's 64
+            for (int m = 0; m < 8; ++m) {
+              const int j2 = blk2 * 8 + m;  // column pair (2 j2, 2 j2 + 1) of the thread's 64
               const uint64_t d1 = D[1][m];
               const uint64_t t1 = sub2(add2(d1, KR2), KR2);
               uint64_t sv = add2(D[0][m], t1);
