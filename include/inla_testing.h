@@ -46,6 +46,11 @@ int64_t inla_test_launch_count(void);
 void inla_test_profile_enable(int on);
 int inla_test_profile_read(char *buf, int len);
 
+/* Dense covariance entries sigma2 * exp(-sqrt((dx * inv_rx)^2 + (dy * inv_ry)^2)) for n <= 8192
+ * host points (row-major n x 2), computed by the mixed path's double-float device code (its own
+ * exp and sqrt on the FP32 pipes) and returned in out (n x n host doubles). */
+int inla_test_cov_df(const double *points, int32_t n, double sigma2, double inv_rx, double inv_ry, double *out);
+
 #ifdef __cplusplus
 }
 #endif

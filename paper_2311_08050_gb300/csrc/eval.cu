@@ -184,14 +184,14 @@ static int op_schur(Batch& B) {
   return INLA_OK;
 }
 static int op_prior_dense(Batch& B) {
-  launch_cov_build(B.d_slots, B.n, B.max_td, B.st);
   if (B.mixed) {
-    launch_cov_to_df(B.d_slots, B.n, B.max_td, B.st);
+    launch_cov_build_df(B.d_slots, B.n, B.max_td, B.st);
     INLA_TRY(mixed_potrf(B, SEL_COV));
     launch_logdet_df(B.d_slots, B.n, SEL_COV, OUT_LOGDET_COV, B.st);
     INLA_TRY(mixed_inverse_factor(B, SEL_COV, false));
     return mixed_lauum_cov(B);
   }
+  launch_cov_build(B.d_slots, B.n, B.max_td, B.st);
   potrf64(B, SEL_COV);
   launch_logdet(B.d_slots, B.n, SEL_COV, OUT_LOGDET_COV, B.st);
   trtri64(B, SEL_COV, DST_L);

@@ -3,6 +3,7 @@
 // factor, log-determinants and column sums of squares.  Arithmetic on the factor runs on
 // the FP32 pipes (df64 operations); vectors and scalars stay FP64 (O(n) work).
 #include "df64.cuh"
+#include "df_exp.cuh"
 #include "device_util.cuh"
 #include "kernels.h"
 #include "mixed.h"
@@ -29,6 +30,74 @@ __device__ __forceinline__ double* vec_ref_df(const Slot& s, int v) {
     case 3: return s.kv1;
     default: return s.kv2;
   }
+}
+
+// Dense covariance block Sigma_ij = sigma^2 exp(-d_ij) (+ the diagonal term), written in
+// double-float straight into Wk (lower tiles; identity on the padding): the distance
+// d = sqrt((dx / rho_x)^2 + (dy / rho_y)^2) and the exponential run in double-float on the
+// FP32 pipes.  The tile's 2 x 64 points are converted once per block (shared memory).
+__device__ __forceinline__ df cov_entry_df(df xi, df yi, df xj, df yj, df irx, df iry, df sigma2) {
+  const df dx = df_mul(df_add(xi, df_neg(xj)), irx);
+  const df dy = df_mul(df_add(yi, df_neg(yj)), iry);
+  const df d2 = df_add(df_mul(dx, dx), df_mul(dy, dy));
+  if (!(d2.hi > 0.f)) return sigma2;
+  return df_mul(sigma2, df_exp_neg(df_sqrt(d2)));
+}
+
+__global__ void __launch_bounds__(256) k_cov_build_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active || s.nd == 0) return;
+  const ModelDev& md = *s.md;
+  int ti, tj;
+  tri_decode(blockIdx.x, ti, tj);
+  if (ti >= s.nd_pad / TB) return;
+  __shared__ float2 px[2][TB], py[2][TB];  // [0]: row points, [1]: column points
+  const double* P = md.points;
+  if (threadIdx.x < 2 * TB) {
+    const int side = threadIdx.x / TB, e = threadIdx.x % TB;
+    const int idx = (side ? tj : ti) * TB + e;
+    df x = df_make(0.f, 0.f), y = df_make(0.f, 0.f);
+    if (idx < s.nd) {
+      x = df_from_double(P[2 * idx]);
+      y = df_from_double(P[2 * idx + 1]);
+    }
+    px[side][e] = make_float2(x.hi, x.lo);
+    py[side][e] = make_float2(y.hi, y.lo);
+  }
+  __syncthreads();
+  const df sigma2 = df_from_double(exp(2.0 * s.theta[md.theta_sigma]));
+  const df irx = df_from_double(exp(-s.theta[md.theta_rx]));
+  const df iry = df_from_double(exp(-s.theta[md.theta_ry]));
+  double diag_add = md.nugget;
+  if (md.theta_iid >= 0) diag_add += exp(-s.theta[md.theta_iid]);
+  const df dadd = df_from_double(diag_add);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int a = e / TB, b = e % TB;
+    const int i = ti * TB + a, j = tj * TB + b;
+    df v;
+    if (i < s.nd && j < s.nd) {
+      v = cov_entry_df(df_make(px[0][a].x, px[0][a].y), df_make(py[0][a].x, py[0][a].y), df_make(px[1][b].x, px[1][b].y),
+                       df_make(py[1][b].x, py[1][b].y), irx, iry, sigma2);
+      if (i == j) v = df_add(v, dadd);
+    } else {
+      v = df_make(i == j ? 1.f : 0.f, 0.f);
+    }
+    df_store(dfm(s.Wk) + (size_t)i * s.n_pad + j, v);
+  }
+}
+
+// test hook support: Sigma entries for raw points (row-major n x 2) in double-float, as FP64
+__global__ void k_cov_points_df(const double* P, int n, double sigma2, double irx, double iry, double* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const df v = cov_entry_df(df_from_double(P[2 * i]), df_from_double(P[2 * i + 1]), df_from_double(P[2 * j]),
+                              df_from_double(P[2 * j + 1]), df_from_double(irx), df_from_double(iry),
+                              df_from_double(sigma2));
+    out[e] = df_to_double(v);
+  }
+}
+void launch_cov_points_df(const double* P, int n, double sigma2, double irx, double iry, double* out, cudaStream_t st) {
+  count_launch("k_cov_points_df"), k_cov_points_df<<<256, 256, 0, st>>>(P, n, sigma2, irx, iry, out);
 }
 
 // in-place FP64 -> df64 on the lower tiles of the dense covariance block (Wk)
@@ -495,6 +564,9 @@ static int vgrid(int n) { return std::min(1024, std::max(1, (n + 255) / 256)); }
 
 void launch_cov_to_df(Slot* slots, int nslots, int max_td, cudaStream_t st) {
   if (max_td > 0) count_launch("k_cov_to_df"), k_cov_to_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
+}
+void launch_cov_build_df(Slot* slots, int nslots, int max_td, cudaStream_t st) {
+  if (max_td > 0) count_launch("k_cov_build_df"), k_cov_build_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
 }
 void launch_prior_entries_df(Slot* slots, int nslots, int64_t max_entries, cudaStream_t st) {
   if (max_entries > 0)

@@ -173,7 +173,7 @@ __device__ __forceinline__ OzTile oz_tile(const OzArgs& p, int t) {
   const int x = t - r.slot * p.tiles_per_slot;
   int tm, tn;
   if (p.lower) {
-    int u = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+    int u = (int)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);  // corrected below (no FP64 on this GPU's hot path)
     while (u * (u + 1) / 2 > x) --u;
     while ((u + 1) * (u + 2) / 2 <= x) ++u;
     tm = u;

@@ -4,6 +4,7 @@
 #include "../../include/inla_testing.h"
 #include "df64.cuh"
 #include "ozaki.h"
+#include "mixed.h"
 
 namespace inla {
 
@@ -103,3 +104,28 @@ extern "C" int inla_test_ozaki_gemm(const double* A, const double* B, double* C,
   if (rc == INLA_E_CUDA) cudaGetLastError();
   return rc;
 }
+
+// Dense covariance entries sigma^2 exp(-sqrt((dx rx^-1)^2 + (dy ry^-1)^2)) of n host points
+// (row-major n x 2) computed by the double-float device code of the mixed path, returned as FP64.
+extern "C" int inla_test_cov_df(const double* points, int32_t n, double sigma2, double inv_rx, double inv_ry,
+                                double* out) {
+  if (!points || !out || n <= 0 || n > 8192) return INLA_E_BADARG;
+  double *dP = nullptr, *dO = nullptr;
+  int rc = INLA_OK;
+  if (cudaMalloc(&dP, sizeof(double) * 2 * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&dO, sizeof(double) * (size_t)n * n) != cudaSuccess)
+    rc = INLA_E_NOMEM;
+  if (rc == INLA_OK && cudaMemcpy(dP, points, sizeof(double) * 2 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = INLA_E_CUDA;
+  if (rc == INLA_OK) {
+    launch_cov_points_df(dP, n, sigma2, inv_rx, inv_ry, dO, 0);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(out, dO, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = INLA_E_CUDA;
+  }
+  cudaFree(dP);
+  cudaFree(dO);
+  if (rc != INLA_OK) cudaGetLastError();
+  return rc;
+}
+

@@ -102,3 +102,32 @@ def test_mixed_config2_subset():
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], sub, precision="mixed")
     _check(spec, sub, lp, st, xs, vs)
+
+
+def test_double_float_covariance_matches_fp64_definition():
+    """The mixed path builds the dense covariance in double-float (its own exp by ln 2
+    reduction and a Taylor series, sqrt by a Newton step): against numpy's FP64 over distances
+    d from 0 to ~40 range units.  exp(-d) has relative condition number d and a double-float
+    distance carries ~2^-46 relative error; the exponential itself (two squarings of a
+    double-float Taylor value) adds ~4 * 2^-46: the bound is (1 + d) * 6e-14 relative, hence
+    sigma^2 (1 + d) e^-d * 6e-14 <= 6e-14 sigma^2 absolute (far below the 2^-35 slice error of
+    the products the covariance enters)."""
+    import ctypes as C
+    L = inla.lib()
+    P = C.POINTER(C.c_double)
+    L.inla_test_cov_df.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_double, P]
+    rng = np.random.default_rng(77)
+    n = 700
+    pts = rng.uniform(0, 1, size=(n, 2))
+    pts[:5] = pts[5]            # coincident points (d = 0)
+    for sigma2, irx, iry in [(1.0, 5.0, 5.0), (2.7, 28.0, 3.0), (0.05, 1.0, 40.0)]:
+        out = np.empty((n, n))
+        rc = L.inla_test_cov_df(pts.ctypes.data_as(P), n, sigma2, irx, iry, out.ctypes.data_as(P))
+        assert rc == 0
+        dx = (pts[:, None, 0] - pts[None, :, 0]) * irx
+        dy = (pts[:, None, 1] - pts[None, :, 1]) * iry
+        d = np.sqrt(dx * dx + dy * dy)
+        ref = sigma2 * np.exp(-d)
+        err = np.abs(out - ref)
+        assert np.max(err / ref / (1.0 + d)) < 6e-14, np.max(err / ref / (1.0 + d))
+        assert np.max(err) / sigma2 < 6e-14, np.max(err) / sigma2
