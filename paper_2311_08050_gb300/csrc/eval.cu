@@ -491,8 +491,8 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
   B.flags = cv.take<int32_t>(G * (np / TB + 1));
   if (L.mixed) {
     const int64_t nch = (int64_t)(np + OZ_CHUNK - 1) / OZ_CHUNK;
-    B.pa_cap = (int64_t)L.S * np * std::max<size_t>(256, kp);
-    B.pb_cap = (int64_t)L.S * np * 256;
+    B.pa_cap = (int64_t)L.S * np * std::max<size_t>(MIXED_NB, kp);
+    B.pb_cap = (int64_t)L.S * np * MIXED_NB;
     B.pbig_cap = (int64_t)L.S * np * np;
     B.ea_cap = nch * (int64_t)std::max<size_t>(np, kp) + np;
     B.eb_cap = nch * (int64_t)np + np;

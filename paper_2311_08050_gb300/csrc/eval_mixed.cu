@@ -1,8 +1,8 @@
 // Blocked dense routines of the mixed path.  Matrices are double-float; every product with a
 // non-trivial K runs on the Ozaki-split tensor-core GEMM; the 64 x 64 diagonal tiles are
-// factored and inverted in double-float.  Two-level blocking: 256-wide outer panels keep the
-// trailing updates' K at one exact accumulation chunk (and C traffic at n^3 / (3 * 256)
-// element updates per factorisation), 64-wide inner steps keep the FP64 work small.
+// factored and inverted in double-float.  Two-level blocking: MIXED_NB-wide outer panels (the
+// trailing updates' K; C traffic n^3 / (3 MIXED_NB) element updates per factorisation), 64-wide
+// inner steps.
 #include "df64.cuh"
 #include "mixed.h"
 
@@ -10,7 +10,7 @@ namespace inla {
 
 namespace {
 
-constexpr int NB = 256;   // outer block
+constexpr int NB = MIXED_NB;   // outer block
 constexpr int IB = TB;    // inner block (64)
 
 struct MRef {

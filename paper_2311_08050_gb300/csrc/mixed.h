@@ -34,6 +34,12 @@ void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st);
 
+// Outer block of the mixed blocked routines: the trailing updates have K = MIXED_NB (C is read
+// and written n^3 / (3 MIXED_NB) times per factorisation).  512 (two exact 256-wide chunks summed
+// in the GEMM's registers) halves that traffic but widens the skinny K = 64 updates inside each
+// outer panel by as much; measured at n = 16384 the two are even, and 256 keeps the workspace small.
+constexpr int MIXED_NB = 256;
+
 // A batch of slots with identical shapes (uniform per-slot strides).
 struct Batch {
   Slot* d_slots;
