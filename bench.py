@@ -102,6 +102,9 @@ def _dist_env():
 
 
 WORKLOADS = {5: "poisson_n16384_m100000_fd9", 2: "poisson_n4096_m20000_fd7", 1: "poisson_n256_m1000_5pts"}
+# ncu capture of the current GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean over
+# all 5613 GEMM launches of one n = 16384 step); retake after any change to the kernel
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = {5: 1.0828e9}
 
 
 def _workload(rank, config=5):
@@ -231,9 +234,13 @@ def run_ours(args):
     peak_tc = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     tens_rate = tens / (kms / 1e3) / 1e12 if kms > 0 else None
     alg_rate = alg / (kms / 1e3) / 1e12 if kms > 0 else None
+    # DRAM bytes per GEMM launch, measured by ncu over every GEMM launch of one step of the
+    # n = 16384 workload (profiles/k_ozaki_gemm_launch_traffic_n16384.md); other workloads: none
+    traffic = GEMM_TRAFFIC_BYTES_PER_LAUNCH.get(args.config)
     roofline = {"bound": "tensor", "kernel": "k_ozaki_gemm<S> (tcgen05 BF16 slices)",
                 "achieved": tens_rate, "peak": peak_tc, "unit": "TFLOP/s",
-                "frac": (tens_rate / peak_tc) if tens_rate else None, "traffic": None,
+                "frac": (tens_rate / peak_tc) if tens_rate else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (dram read + write, ncu)" if traffic else None,
                 "algorithmic_tflops": alg_rate, "passes_per_flop": round(tens / alg, 2) if alg else None,
                 "launches_per_step": int(launches), "kernel_ms_per_step": kms,
                 "peak_source": f"{psrc} bf16 sustained (kernel timed inside a long step)"}
