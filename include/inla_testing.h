@@ -51,6 +51,11 @@ int inla_test_profile_read(char *buf, int len);
  * exp and sqrt on the FP32 pipes) and returned in out (n x n host doubles). */
 int inla_test_cov_df(const double *points, int32_t n, double sigma2, double inv_rx, double inv_ry, double *out);
 
+/* The last batch's Newton iterations (this host thread's most recent inla_eval_batch): for each
+ * iteration the largest step over the points still iterating and whether the factor was
+ * computed afresh (1) or reused (0).  Writes up to cap entries; returns the iteration count. */
+int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
+
 #ifdef __cplusplus
 }
 #endif

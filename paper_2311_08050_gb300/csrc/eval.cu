@@ -26,6 +26,12 @@ void launch_gather(double* dst, const double* src, const int32_t* perm, int n, c
 
 int64_t g_kernel_launches = 0;
 static char g_debug_site[256] = "";
+// last batch's Newton iterations: largest step over the active points, fresh factor or reused
+struct NewtonTraceEntry {
+  double step;
+  int refactored;
+};
+static std::vector<NewtonTraceEntry> g_newton_trace;
 bool debug_sync_enabled() {
   static int on = -1;
   if (on < 0) {
@@ -295,6 +301,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   int rc = INLA_OK;
   double last_step = 1e300;
   bool reuse_ok = true;
+  g_newton_trace.clear();
   for (int it = 1; it <= o.newton_max && rc == INLA_OK; ++it) {
     int nact = 0;
     for (int i = 0; i < NB; ++i) nact += B.h[i].active;
@@ -355,6 +362,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
         if (B.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
       reuse_ok = refactor || mx < 0.25 * last_step;
       last_step = mx;
+      g_newton_trace.push_back({mx, refactor ? 1 : 0});
     }
     for (int i = 0; i < NB; ++i) {
       if (!B.h[i].active) continue;
@@ -774,3 +782,13 @@ extern "C" const char* inla_status_string(int s) {
     default: return "unknown status";
   }
 }
+
+extern "C" int inla_test_newton_trace(double* steps, int32_t* refactored, int32_t cap) {
+  const int n = (int)g_newton_trace.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (steps) steps[i] = g_newton_trace[i].step;
+    if (refactored) refactored[i] = g_newton_trace[i].refactored;
+  }
+  return n;
+}
+

@@ -131,3 +131,28 @@ def test_double_float_covariance_matches_fp64_definition():
         err = np.abs(out - ref)
         assert np.max(err / ref / (1.0 + d)) < 6e-14, np.max(err / ref / (1.0 + d))
         assert np.max(err) / sigma2 < 6e-14, np.max(err) / sigma2
+
+
+def test_newton_trace_refactors_early_and_reuses_near_the_mode():
+    """The mixed Newton iteration (Algorithm 1 with a fresh factor while the steps are large)
+    reuses the factor once steps are small and shrinking (modified Newton: the gradient is
+    exact, so the fixed point is the mode); the FP64 path refactors every iteration.  Both reach
+    the step tolerance."""
+    import ctypes as C
+    L = inla.lib()
+    L.inla_test_newton_trace.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+    spec, thetas = synth.CONFIGS[1]()
+    model = inla.Model(spec)
+    for prec in ("mixed", "fp64"):
+        inla.eval_batch([model], thetas, want_x=False, want_var=False, precision=prec)
+        steps = np.zeros(64)
+        ref = np.zeros(64, dtype=np.int32)
+        n = L.inla_test_newton_trace(steps.ctypes.data_as(C.POINTER(C.c_double)),
+                                     ref.ctypes.data_as(C.POINTER(C.c_int32)), 64)
+        assert 2 <= n <= 50
+        assert ref[0] == 1 and ref[1] == 1
+        assert steps[n - 1] <= 1e-8
+        if prec == "fp64":
+            assert np.all(ref[:n] == 1)
+        else:
+            assert ref[n - 1] == 0       # the last iterations reuse the factor
