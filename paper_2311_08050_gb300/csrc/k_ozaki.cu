@@ -29,12 +29,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
+// Bounded wait for a phase; try_wait with a short (32 ns) suspend-time hint: the hand-offs
+// between the MMA issuer and the epilogue then resume promptly.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int64_t limit) {
   const uint32_t a = smem_u32(bar);
   for (int64_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 32; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
         : "r"(a), "r"(parity)
         : "memory");
