@@ -1,6 +1,7 @@
 """Mixed-precision path (double-float storage, Ozaki-split tcgen05 GEMMs: 5 slices for the prior
-inversion and the factor at the mode, 4 for the Newton factorisations,
-FP64 64 x 64 diagonal tiles) against the FP64 oracle.
+inversion and the factor at the mode, 4 for the Newton factorisations, double-float 64 x 64
+diagonal tiles) against the FP64 oracle, and at full size against the FP64 GPU path (itself
+pinned to the oracle by test_gpu_parity.py).
 
 Tolerances are the stated targets for the mixed form: |log pi~ - oracle| <= 1e-3 and the
 marginal variances within 1e-4 relative.  The mode is the fixed point of Newton steps whose
@@ -156,3 +157,43 @@ def test_newton_trace_refactors_early_and_reuses_near_the_mode():
             assert np.all(ref[:n] == 1)
         else:
             assert ref[n - 1] == 0       # the last iterations reuse the factor
+
+
+def _check_vs_fp64(lp, st, xs, vs, ref, names):
+    lp64, st64, xs64, vs64 = ref
+    for b in range(len(lp)):
+        assert st[b] == 0 and st64[b] == 0, (names[b], inla.status_string(st[b]), inla.status_string(st64[b]))
+        e_lp = abs(lp[b] - lp64[b])
+        e_x = np.max(np.abs(xs[b] - xs64[b])) / max(1.0, np.max(np.abs(xs64[b])))
+        e_v = np.max(np.abs(vs[b] / vs64[b] - 1))
+        assert e_lp <= LP_ABS, (names[b], e_lp)
+        assert e_x <= X_RTOL, (names[b], e_x)
+        assert e_v <= V_RTOL, (names[b], e_v)
+
+
+@pytest.mark.slow
+def test_mixed_config3_full_size_against_fp64_path():
+    """The constrained space-time model at full size (n = 8149, k = 1486 sum-to-zero
+    constraints, six log precisions): two FD points, mixed against FP64 on the GPU."""
+    spec, thetas = synth.config3()
+    sub = thetas[[0, 7]]
+    m = inla.Model(spec)
+    mixed = inla.eval_batch([m], sub, precision="mixed")
+    fp64 = inla.eval_batch([m], sub, precision="fp64")
+    _check_vs_fp64(*mixed, fp64, ["fd0", "fd7"])
+    C = spec.C.to_dense()
+    for x in mixed[2]:
+        assert np.max(np.abs(C @ x)) < 1e-6
+
+
+@pytest.mark.slow
+def test_mixed_config4_all_uneven_models_against_fp64_path():
+    """All 64 Gaussian models of uneven size (n in {512, 1024, 2048, 4096}) in one batch call,
+    each at its own theta: mixed against FP64 on the GPU, model by model."""
+    specs, thetas = synth.config4()
+    ms = [inla.Model(sp) for sp in specs]
+    which = np.arange(len(specs), dtype=np.int32)
+    mixed = inla.eval_batch(ms, thetas, model_of_theta=which, precision="mixed")
+    fp64 = inla.eval_batch(ms, thetas, model_of_theta=which, precision="fp64")
+    _check_vs_fp64(*mixed, fp64, [sp.name for sp in specs])
+
