@@ -70,6 +70,7 @@ static std::mutex g_mutex;
 
 static int arena_reserve(size_t bytes, int device) {
   if (g_arena.base && g_arena.size >= bytes && g_arena.device == device) return INLA_OK;
+  mixed_graphs_clear();  // captured graphs hold pointers into the old workspace
   if (g_arena.base) {
     cudaFree(g_arena.base);
     g_arena.base = nullptr;

@@ -3,6 +3,7 @@
 // factored and inverted in double-float.  Two-level blocking: MIXED_NB-wide outer panels (the
 // trailing updates' K; C traffic n^3 / (3 MIXED_NB) element updates per factorisation), 64-wide
 // inner steps.
+#include <map>
 #include "df64.cuh"
 #include "mixed.h"
 
@@ -61,8 +62,8 @@ OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, in
 
 }  // namespace
 
-// In-place Cholesky of the matrix selected by `sel` (lower triangle), every slot.
-int mixed_potrf(Batch& B, int sel) {
+// In-place Cholesky of the matrix selected by `sel` (lower triangle), every slot: the launches.
+static int mixed_potrf_launches(Batch& B, int sel) {
   const MRef M = mref(B, sel);
   const int n = M.n, S = B.S;
   for (int K0 = 0; K0 < n; K0 += NB) {
@@ -100,6 +101,82 @@ int mixed_potrf(Batch& B, int sel) {
       INLA_TRY(oz_gemm(pp, pp, a, B.n, B.st));
     }
   }
+  return INLA_OK;
+}
+
+// The blocked Cholesky issues ~1700 launches at n = 16384 whose sequence depends only on the
+// batch layout (buffers, strides, slot count), the matrix selected and the slice count.  The
+// first call with a layout runs the launches; the second captures them into a CUDA graph
+// (stream capture, this thread only) and every later call replays it.  Off when the per-kernel
+// profiler, the GEMM statistics or debug synchronisation is on, or on the legacy default stream
+// (which cannot be captured).
+namespace {
+struct PotrfGraphKey {
+  int sel, S, n_slots;
+  const void* ptrs[7];
+  int64_t spin;
+  bool operator<(const PotrfGraphKey& o) const {
+    if (sel != o.sel) return sel < o.sel;
+    if (S != o.S) return S < o.S;
+    if (n_slots != o.n_slots) return n_slots < o.n_slots;
+    if (spin != o.spin) return spin < o.spin;
+    for (int i = 0; i < 7; ++i)
+      if (ptrs[i] != o.ptrs[i]) return ptrs[i] < o.ptrs[i];
+    return false;
+  }
+};
+struct PotrfGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  bool failed = false;
+};
+std::map<PotrfGraphKey, PotrfGraph> g_potrf_graphs;
+}  // namespace
+
+void mixed_graphs_clear() {
+  for (auto& kv : g_potrf_graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  g_potrf_graphs.clear();
+}
+
+int mixed_potrf(Batch& B, int sel) {
+  if (B.st == nullptr || prof_active() || oz_stats_active() || debug_sync_enabled()) return mixed_potrf_launches(B, sel);
+  const MRef M = mref(B, sel);
+  PotrfGraphKey key{sel, B.S, B.n, {B.d_slots, M.base, M.linv, B.PA, B.PB, B.EA, B.err}, B.spin_limit};
+  auto it = g_potrf_graphs.find(key);
+  if (it == g_potrf_graphs.end()) {
+    if (g_potrf_graphs.size() >= 32) mixed_graphs_clear();
+    g_potrf_graphs[key] = PotrfGraph{};
+    return mixed_potrf_launches(B, sel);  // first use of this layout: plain launches
+  }
+  PotrfGraph& g = it->second;
+  if (g.failed) return mixed_potrf_launches(B, sel);
+  if (!g.exec) {
+    cudaGraph_t graph = nullptr;
+    const int64_t c0 = g_kernel_launches;
+    int rc = INLA_OK;
+    if (cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g.failed = true;
+      return mixed_potrf_launches(B, sel);
+    }
+    rc = mixed_potrf_launches(B, sel);
+    const cudaError_t e = cudaStreamEndCapture(B.st, &graph);
+    if (rc != INLA_OK || e != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      g.exec = nullptr;
+      g.failed = true;
+      g_kernel_launches = c0;
+      return mixed_potrf_launches(B, sel);  // nothing ran during the capture
+    }
+    cudaGraphDestroy(graph);
+    g.launches = g_kernel_launches - c0;
+    g_kernel_launches = c0;
+  }
+  if (cudaGraphLaunch(g.exec, B.st) != cudaSuccess) return note_launch_error("mixed potrf graph launch");
+  g_kernel_launches += g.launches;
   return INLA_OK;
 }
 

@@ -678,6 +678,7 @@ struct OzStats {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 static OzStats g_stats;
+bool oz_stats_active() { return g_stats.on; }
 
 static double oz_alg_flops(const OzArgs& a, int nslots) {
   double f = 0.0;

@@ -66,7 +66,8 @@ struct Batch {
 };
 
 // mixed blocked routines (eval_mixed.cu)
-int mixed_potrf(Batch& B, int sel);
+int mixed_potrf(Batch& B, int sel);          // replays a captured CUDA graph for a known layout
+void mixed_graphs_clear();                   // drop every captured graph (workspace reallocated)
 int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // W = F^-1 (lower), F by sel
 int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = W^T W (W in L)
 int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S

@@ -22,6 +22,7 @@ Prof g_prof;
 }  // namespace
 
 void prof_set_stream(cudaStream_t st) { g_prof.st = st; }
+bool prof_active() { return g_prof.on; }
 
 int count_launch(const char* name) {
   ++g_kernel_launches;
