@@ -103,8 +103,9 @@ def _dist_env():
 
 WORKLOADS = {5: "poisson_n16384_m100000_fd9", 2: "poisson_n4096_m20000_fd7", 1: "poisson_n256_m1000_5pts"}
 # ncu capture of the current GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean over
-# all 5613 GEMM launches of one n = 16384 step); retake after any change to the kernel
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = {5: 1.0828e9}
+# all 5613 GEMM launches of one n = 16384 step, outer block 512 as tuned); retake after any change
+# to the kernel or the blocking
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = {5: 0.9145e9}
 
 
 def _workload(rank, config=5):
@@ -237,6 +238,8 @@ def run_ours(args):
     # DRAM bytes per GEMM launch, measured by ncu over every GEMM launch of one step of the
     # n = 16384 workload (profiles/k_ozaki_gemm_launch_traffic_n16384.md); other workloads: none
     traffic = GEMM_TRAFFIC_BYTES_PER_LAUNCH.get(args.config)
+    n_pad = ((spec.n + 255) // 256) * 256
+    outer_block = {f"slices{sl}": int(L.inla_test_outer_block(n_pad, sl)) for sl in (args.newton_slices, args.slices)}
     roofline = {"bound": "tensor", "kernel": "k_ozaki_gemm<S> (tcgen05 BF16 slices)",
                 "achieved": tens_rate, "peak": peak_tc, "unit": "TFLOP/s",
                 "frac": (tens_rate / peak_tc) if tens_rate else None, "traffic": traffic,
@@ -254,6 +257,7 @@ def run_ours(args):
            "config": {"workload": WORKLOADS[args.config], "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
                       "precision": args.precision, "slices": args.slices,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
+                      "outer_block_tuned": outer_block,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
            "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
            "kernel_breakdown": breakdown[:12]}

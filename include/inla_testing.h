@@ -56,6 +56,11 @@ int inla_test_cov_df(const double *points, int32_t n, double sigma2, double inv_
  * computed afresh (1) or reused (0).  Writes up to cap entries; returns the iteration count. */
 int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
 
+/* The outer block (panel width) the mixed Cholesky chose for matrices of padded size n_pad
+ * factored with `slices` slices: 256 or 512 once its two timed candidate runs are complete,
+ * 0 while undecided (sizes below 1024 always use 256). */
+int inla_test_outer_block(int32_t n_pad, int32_t slices);
+
 #ifdef __cplusplus
 }
 #endif

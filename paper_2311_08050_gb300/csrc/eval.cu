@@ -500,8 +500,8 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
   B.flags = cv.take<int32_t>(G * (np / TB + 1));
   if (L.mixed) {
     const int64_t nch = (int64_t)(np + OZ_CHUNK - 1) / OZ_CHUNK;
-    B.pa_cap = (int64_t)L.S * np * std::max<size_t>(MIXED_NB, kp);
-    B.pb_cap = (int64_t)L.S * np * MIXED_NB;
+    B.pa_cap = (int64_t)L.S * np * std::max<size_t>(MIXED_NB_MAX, kp);
+    B.pb_cap = (int64_t)L.S * np * MIXED_NB_MAX;
     B.pbig_cap = (int64_t)L.S * np * np;
     B.ea_cap = nch * (int64_t)std::max<size_t>(np, kp) + np;
     B.eb_cap = nch * (int64_t)np + np;
@@ -792,4 +792,6 @@ extern "C" int inla_test_newton_trace(double* steps, int32_t* refactored, int32_
   }
   return n;
 }
+
+extern "C" int inla_test_outer_block(int32_t n_pad, int32_t slices) { return mixed_nb_choice(n_pad, slices); }
 

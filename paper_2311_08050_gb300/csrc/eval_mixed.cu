@@ -1,8 +1,8 @@
 // Blocked dense routines of the mixed path.  Matrices are double-float; every product with a
 // non-trivial K runs on the Ozaki-split tensor-core GEMM; the 64 x 64 diagonal tiles are
-// factored and inverted in double-float.  Two-level blocking: MIXED_NB-wide outer panels (the
-// trailing updates' K; C traffic n^3 / (3 MIXED_NB) element updates per factorisation), 64-wide
-// inner steps.
+// factored and inverted in double-float.  Two-level blocking: outer panels of NB columns (the
+// trailing updates' K; C traffic n^3 / (3 NB) element updates per factorisation; NB tuned per
+// matrix size for the Cholesky), 64-wide inner steps.
 #include <map>
 #include "df64.cuh"
 #include "mixed.h"
@@ -11,7 +11,7 @@ namespace inla {
 
 namespace {
 
-constexpr int NB = MIXED_NB;   // outer block
+constexpr int NB = MIXED_NB;   // outer block of the triangular solves
 constexpr int IB = TB;    // inner block (64)
 
 struct MRef {
@@ -63,11 +63,11 @@ OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, in
 }  // namespace
 
 // In-place Cholesky of the matrix selected by `sel` (lower triangle), every slot: the launches.
-static int mixed_potrf_launches(Batch& B, int sel) {
+static int mixed_potrf_launches(Batch& B, int sel, int nb) {
   const MRef M = mref(B, sel);
   const int n = M.n, S = B.S;
-  for (int K0 = 0; K0 < n; K0 += NB) {
-    const int kend = std::min(K0 + NB, n);
+  for (int K0 = 0; K0 < n; K0 += nb) {
+    const int kend = std::min(K0 + nb, n);
     for (int j0 = K0; j0 < kend; j0 += IB) {
       launch_potrf_diag_df(B.d_slots, B.n, sel, j0 / IB, B.st);
       const int R = n - j0 - IB;
@@ -112,13 +112,14 @@ static int mixed_potrf_launches(Batch& B, int sel) {
 // (which cannot be captured).
 namespace {
 struct PotrfGraphKey {
-  int sel, S, n_slots;
+  int sel, S, n_slots, nb;
   const void* ptrs[7];
   int64_t spin;
   bool operator<(const PotrfGraphKey& o) const {
     if (sel != o.sel) return sel < o.sel;
     if (S != o.S) return S < o.S;
     if (n_slots != o.n_slots) return n_slots < o.n_slots;
+    if (nb != o.nb) return nb < o.nb;
     if (spin != o.spin) return spin < o.spin;
     for (int i = 0; i < 7; ++i)
       if (ptrs[i] != o.ptrs[i]) return ptrs[i] < o.ptrs[i];
@@ -139,18 +140,76 @@ void mixed_graphs_clear() {
   g_potrf_graphs.clear();
 }
 
+// Outer-block tuner: for each (matrix size, slices) the first factorisation runs with each
+// candidate in turn, timed with CUDA events on the stream (the factorisations are the real ones:
+// no extra work); once both timings are complete, the faster candidate is used from then on.
+namespace {
+constexpr int kNbCandidates[2] = {256, 512};
+struct NbTune {
+  cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int runs = 0;
+  int best = 0;  // 0: undecided
+};
+std::map<std::pair<int, int>, NbTune> g_nb_tune;
+
+int pick_nb(const MRef& M, int S, NbTune*& tune, int& cand) {
+  tune = nullptr;
+  cand = -1;
+  if (M.n < 2 * kNbCandidates[1]) return kNbCandidates[0];  // too small for the wider panel to matter
+  NbTune& t = g_nb_tune[{M.n, S}];
+  if (t.best) return t.best;
+  if (t.runs == 2) {
+    float ms[2] = {0.f, 0.f};
+    bool done = true;
+    for (int c = 0; c < 2; ++c)
+      done = done && cudaEventQuery(t.ev[c][1]) == cudaSuccess &&
+             cudaEventElapsedTime(&ms[c], t.ev[c][0], t.ev[c][1]) == cudaSuccess;
+    cudaGetLastError();
+    if (done) {
+      t.best = ms[1] < ms[0] ? kNbCandidates[1] : kNbCandidates[0];
+      for (auto& e2 : t.ev)
+        for (auto& e : e2) cudaEventDestroy(e);
+      return t.best;
+    }
+    return kNbCandidates[0];  // timings not complete yet
+  }
+  cand = t.runs;
+  tune = &t;
+  return kNbCandidates[cand];
+}
+}  // namespace
+
+int mixed_nb_choice(int n, int S) {
+  auto it = g_nb_tune.find({n, S});
+  return it == g_nb_tune.end() ? 0 : it->second.best;
+}
+
 int mixed_potrf(Batch& B, int sel) {
-  if (B.st == nullptr || prof_active() || oz_stats_active() || debug_sync_enabled()) return mixed_potrf_launches(B, sel);
   const MRef M = mref(B, sel);
-  PotrfGraphKey key{sel, B.S, B.n, {B.d_slots, M.base, M.linv, B.PA, B.PB, B.EA, B.err}, B.spin_limit};
+  NbTune* tune = nullptr;
+  int cand = -1;
+  const int nb = pick_nb(M, B.S, tune, cand);
+  if (tune) {
+    // a tuning run: timed, never captured
+    for (auto& e : tune->ev[cand])
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return INLA_E_CUDA;
+    cudaEventRecord(tune->ev[cand][0], B.st);
+    const int rc = mixed_potrf_launches(B, sel, nb);
+    cudaEventRecord(tune->ev[cand][1], B.st);
+    ++tune->runs;
+    return rc;
+  }
+  if (B.st == nullptr || prof_active() || oz_stats_active() || debug_sync_enabled())
+    return mixed_potrf_launches(B, sel, nb);
+  PotrfGraphKey key{sel, B.S, B.n, nb, {B.d_slots, M.base, M.linv, B.PA, B.PB, B.EA, B.err}, B.spin_limit};
   auto it = g_potrf_graphs.find(key);
   if (it == g_potrf_graphs.end()) {
     if (g_potrf_graphs.size() >= 32) mixed_graphs_clear();
     g_potrf_graphs[key] = PotrfGraph{};
-    return mixed_potrf_launches(B, sel);  // first use of this layout: plain launches
+    return mixed_potrf_launches(B, sel, nb);  // first use of this layout: plain launches
   }
   PotrfGraph& g = it->second;
-  if (g.failed) return mixed_potrf_launches(B, sel);
+  if (g.failed) return mixed_potrf_launches(B, sel, nb);
   if (!g.exec) {
     cudaGraph_t graph = nullptr;
     const int64_t c0 = g_kernel_launches;
@@ -158,9 +217,9 @@ int mixed_potrf(Batch& B, int sel) {
     if (cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       g.failed = true;
-      return mixed_potrf_launches(B, sel);
+      return mixed_potrf_launches(B, sel, nb);
     }
-    rc = mixed_potrf_launches(B, sel);
+    rc = mixed_potrf_launches(B, sel, nb);
     const cudaError_t e = cudaStreamEndCapture(B.st, &graph);
     if (rc != INLA_OK || e != cudaSuccess || !graph ||
         cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
@@ -169,7 +228,7 @@ int mixed_potrf(Batch& B, int sel) {
       g.exec = nullptr;
       g.failed = true;
       g_kernel_launches = c0;
-      return mixed_potrf_launches(B, sel);  // nothing ran during the capture
+      return mixed_potrf_launches(B, sel, nb);  // nothing ran during the capture
     }
     cudaGraphDestroy(graph);
     g.launches = g_kernel_launches - c0;

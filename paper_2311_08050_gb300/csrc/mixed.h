@@ -34,11 +34,13 @@ void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st);
 
-// Outer block of the mixed blocked routines: the trailing updates have K = MIXED_NB (C is read
-// and written n^3 / (3 MIXED_NB) times per factorisation).  512 (two exact 256-wide chunks summed
+// Outer block of the mixed blocked routines: the trailing updates have K = outer block (C is
+// read and written n^3 / (3 NB) times per factorisation).  512 (two exact 256-wide chunks summed
 // in the GEMM's registers) halves that traffic but widens the skinny K = 64 updates inside each
-// outer panel by as much; measured at n = 16384 the two are even, and 256 keeps the workspace small.
+// outer panel; the Cholesky picks between the candidates per matrix size (mixed_potrf's tuner),
+// the triangular solves use MIXED_NB.
 constexpr int MIXED_NB = 256;
+constexpr int MIXED_NB_MAX = 512;   // workspace capacity (largest candidate)
 
 // A batch of slots with identical shapes (uniform per-slot strides).
 struct Batch {
@@ -68,6 +70,7 @@ struct Batch {
 // mixed blocked routines (eval_mixed.cu)
 int mixed_potrf(Batch& B, int sel);          // replays a captured CUDA graph for a known layout
 void mixed_graphs_clear();                   // drop every captured graph (workspace reallocated)
+int mixed_nb_choice(int n, int S);           // the tuned outer block for (n, S), 0 if undecided
 int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // W = F^-1 (lower), F by sel
 int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = W^T W (W in L)
 int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S

@@ -197,3 +197,21 @@ def test_mixed_config4_all_uneven_models_against_fp64_path():
     fp64 = inla.eval_batch(ms, thetas, model_of_theta=which, precision="fp64")
     _check_vs_fp64(*mixed, fp64, [sp.name for sp in specs])
 
+
+def test_outer_block_tuner_decides_and_results_agree():
+    """The mixed Cholesky times its two outer-block candidates (256, 512) on the first two real
+    factorisations of a size and keeps the faster; every result along the way (both candidates
+    and the tuned choice) stays within the mixed tolerances of the oracle."""
+    import ctypes as C
+    L = inla.lib()
+    spec = synth.spatial_poisson("tune_n1500", synth.SEED_BASE + 71, 1499, 4000, [0.0, np.log(0.2)])
+    thetas = np.array([[0.0, np.log(0.2)], [0.3, np.log(0.15)]])
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
+    _check(spec, thetas, lp, st, xs, vs)
+    lp2, st2, xs2, vs2 = inla.eval_batch([m], thetas, precision="mixed")
+    _check(spec, thetas, lp2, st2, xs2, vs2)
+    n_pad = 1536
+    assert L.inla_test_outer_block(n_pad, 4) in (256, 512)
+    assert L.inla_test_outer_block(n_pad, 5) in (256, 512)
+
