@@ -100,20 +100,6 @@ void launch_cov_points_df(const double* P, int n, double sigma2, double irx, dou
   count_launch("k_cov_points_df"), k_cov_points_df<<<256, 256, 0, st>>>(P, n, sigma2, irx, iry, out);
 }
 
-// in-place FP64 -> df64 on the lower tiles of the dense covariance block (Wk)
-__global__ void __launch_bounds__(256) k_cov_to_df(Slot* slots) {
-  const Slot& s = slots[blockIdx.y];
-  if (!s.active || s.nd == 0) return;
-  int ti, tj;
-  tri_decode(blockIdx.x, ti, tj);
-  if (ti >= s.nd_pad / TB) return;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    double* p = s.Wk + (size_t)(ti * TB + e / TB) * s.n_pad + tj * TB + e % TB;
-    const df v = df_from_double(*p);
-    *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo);
-  }
-}
-
 __global__ void k_prior_entries_df(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
@@ -202,21 +188,6 @@ __global__ void k_s_pad_identity(Slot* slots) {
   if (!s.active || s.k == 0) return;
   for (int r = s.k + blockIdx.x * 256 + threadIdx.x; r < s.k_pad; r += gridDim.x * 256)
     df_store(dfm(s.S) + (size_t)r * s.k_pad + r, df_make(1.f, 0.f));
-}
-
-// identity on the lower triangle of an n_pad x n_pad df64 matrix (W before the inverse)
-__global__ void __launch_bounds__(256) k_set_identity_df(Slot* slots, int which_wk, int size_sel) {
-  const Slot& s = slots[blockIdx.y];
-  if (!s.active) return;
-  const int n = size_sel == SEL_COV ? s.nd_pad : s.n_pad;
-  int ti, tj;
-  tri_decode(blockIdx.x, ti, tj);
-  if (ti >= n / TB) return;
-  float2* W = dfm(which_wk ? s.Wk : s.L);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int r = ti * TB + e / TB, c = tj * TB + e % TB;
-    W[(size_t)r * s.n_pad + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
-  }
 }
 
 // Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
@@ -562,9 +533,6 @@ __global__ void __launch_bounds__(256) k_colsumsq_gt_df(Slot* slots) {
 static int tri(int t) { return t * (t + 1) / 2; }
 static int vgrid(int n) { return std::min(1024, std::max(1, (n + 255) / 256)); }
 
-void launch_cov_to_df(Slot* slots, int nslots, int max_td, cudaStream_t st) {
-  if (max_td > 0) count_launch("k_cov_to_df"), k_cov_to_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
-}
 void launch_cov_build_df(Slot* slots, int nslots, int max_td, cudaStream_t st) {
   if (max_td > 0) count_launch("k_cov_build_df"), k_cov_build_df<<<dim3(tri(max_td), nslots), 256, 0, st>>>(slots);
 }
@@ -588,9 +556,6 @@ void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st) {
 }
 void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st) {
   count_launch("k_s_pad_identity"), k_s_pad_identity<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
-}
-void launch_set_identity_df(Slot* slots, int nslots, int which_wk, int size_sel, int max_t, cudaStream_t st) {
-  count_launch("k_set_identity_df"), k_set_identity_df<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots, which_wk, size_sel);
 }
 void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st) {
   count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, 0, st>>>(slots, sel, kt);

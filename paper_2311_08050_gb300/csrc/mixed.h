@@ -7,7 +7,6 @@
 namespace inla {
 
 // ---- k_df.cu launchers ----
-void launch_cov_to_df(Slot* slots, int nslots, int max_td, cudaStream_t st);
 void launch_cov_build_df(Slot* slots, int nslots, int max_td, cudaStream_t st);
 void launch_cov_points_df(const double* P, int n, double sigma2, double irx, double iry, double* out, cudaStream_t st);
 void launch_prior_entries_df(Slot* slots, int nslots, int64_t max_entries, cudaStream_t st);
