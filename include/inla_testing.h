@@ -37,6 +37,11 @@ const char *inla_test_debug_site(void);
 void inla_test_stats_enable(int on);
 int inla_test_stats_read(double *out);
 
+/* Tile width of the Ozaki-split GEMM: 0 (default) chooses by shape -- the double-buffered
+ * 128 x 64 tile for products of at most 64 columns or with K <= 64, 128 x 128 otherwise; 64 or 128 forces
+ * one for every later launch.  INLA_E_BADARG for any other value. */
+int inla_test_gemm_tile_width(int bn);
+
 /* Number of CUDA kernels the library launched since the previous call (then reset). */
 int64_t inla_test_launch_count(void);
 

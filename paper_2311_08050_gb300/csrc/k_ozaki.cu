@@ -1,12 +1,14 @@
 // tcgen05 / TMA implementation of the Ozaki-split GEMM declared in ozaki.h.
 //
-// Persistent kernel: one CTA per SM walks 128 x 128 output tiles (slot-major) with 12 warps
-// (warpgroup 0 gives registers up to warpgroups 1-2 with setmaxnreg):
+// Persistent kernel: one CTA per SM walks 128 x BN output tiles (slot-major; BN = 128, or 64
+// for narrow or short-K products) with 12 warps (warpgroup 0 gives registers up to warpgroups
+// 1-2 with setmaxnreg):
 //   warp 0      TMA producer: a stage is the S slices of A and of B for 32 values of k
-//               (two 3-D boxes, 64-byte swizzle); 2..6 stages depending on S;
-//   warp 1      owns the TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=128, K=16,
+//               (two 3-D boxes, 64-byte swizzle); 2..6 stages depending on S and BN;
+//   warp 1      owns the TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=BN, K=16,
 //               BF16 x BF16 -> FP32) into min(S, 4) accumulators, slice-order d = i + j
-//               (groups d >= 3 share the last one);
+//               (groups d >= 3 share the last one); with BN = 64 two accumulator sets
+//               alternate by chunk, so the MMAs run on while the epilogue reads the other set;
 //   warps 4..11 epilogue: after each 256-wide K chunk, read the accumulators (tcgen05.ld),
 //               combine them in double-float, scale by 2^(eA + eB - 14) and add the chunk
 //               into a register tile, then release the TMEM so that the next chunk (or tile)
@@ -69,15 +71,25 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 // Pipeline geometry: a stage holds the S slices of both operands for OZ_KS values of k;
-// the stage count fills the shared memory left after the epilogue staging buffers.
-template <int S>
+// the stage count fills the shared memory left after the epilogue staging buffers.  The TMEM
+// holds NBUF sets of NACC accumulators of BN columns: with two sets (the narrow tile) the MMAs
+// of the next chunk run while the epilogue reads the previous one.
+template <int S, int BN>
 struct OzCfg {
-  static constexpr int STAGE_BYTES = 2 * S * OZ_SLICE_BYTES;
+  static constexpr int A_SLICE = OZ_BM * OZ_KS * 2;
+  static constexpr int B_SLICE = BN * OZ_KS * 2;
+  static constexpr int STAGE_BYTES = S * (A_SLICE + B_SLICE);
   static constexpr int NST_FIT = (OZ_SMEM_BUDGET - 1024 - OZ_STAGING_BYTES - OZ_COLSC_BYTES) / STAGE_BYTES;
   static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
   static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OZ_STAGING_BYTES + OZ_COLSC_BYTES;  // 1024: alignment
   static constexpr int NACC = S < OZ_NACC ? S : OZ_NACC;
-  static constexpr uint32_t TMEM_COLS = NACC * OZ_BN <= 256 ? 256 : 512;
+  static constexpr int ACC_COLS = NACC * BN;                 // one accumulator set
+  static constexpr int NBUF = 2 * ACC_COLS <= 512 ? 2 : 1;
+  static constexpr int USED = NBUF * ACC_COLS;
+  static constexpr uint32_t TMEM_COLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
+  static constexpr int CPT = BN / 2;                         // columns per epilogue thread
+  static_assert(BN == OZ_BN || BN == OZ_BN_NARROW, "tile width");
+  static_assert(STAGE_BYTES % 1024 == 0, "stages keep the 64-byte swizzle atoms aligned");
 };
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
@@ -120,13 +132,13 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
-// Load 16 consecutive TMEM columns of NA accumulators (columns col + a * OZ_BN), wait for the
+// Load 16 consecutive TMEM columns of NA accumulators (columns col + a * stride), wait for the
 // loads, and return them as packed column pairs d[a][m] = (column 2m, column 2m + 1).  One asm
 // statement: the registers are read only after tcgen05.wait::ld.
 template <int NA>
-__device__ __forceinline__ void tmem_ld16_pairs(uint32_t taddr, uint64_t (&d)[NA][8]);
+__device__ __forceinline__ void tmem_ld16_pairs(uint32_t taddr, uint32_t stride, uint64_t (&d)[NA][8]);
 template <>
-__device__ __forceinline__ void tmem_ld16_pairs<2>(uint32_t t, uint64_t (&d)[2][8]) {
+__device__ __forceinline__ void tmem_ld16_pairs<2>(uint32_t t, uint32_t stride, uint64_t (&d)[2][8]) {
   asm volatile(
       "{\n.reg .b32 a<32>;\n"
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%16];\n"
@@ -134,11 +146,11 @@ __device__ __forceinline__ void tmem_ld16_pairs<2>(uint32_t t, uint64_t (&d)[2][
       "tcgen05.wait::ld.sync.aligned;\n"
       "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31};\n}"
       : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7])
-      : "r"(t), "r"(t + 1 * OZ_BN)
+      : "r"(t), "r"(t + 1 * stride)
       : "memory");
 }
 template <>
-__device__ __forceinline__ void tmem_ld16_pairs<3>(uint32_t t, uint64_t (&d)[3][8]) {
+__device__ __forceinline__ void tmem_ld16_pairs<3>(uint32_t t, uint32_t stride, uint64_t (&d)[3][8]) {
   asm volatile(
       "{\n.reg .b32 a<48>;\n"
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%24];\n"
@@ -147,11 +159,11 @@ __device__ __forceinline__ void tmem_ld16_pairs<3>(uint32_t t, uint64_t (&d)[3][
       "tcgen05.wait::ld.sync.aligned;\n"
       "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31}; mov.b64 %16, {a32,a33}; mov.b64 %17, {a34,a35}; mov.b64 %18, {a36,a37}; mov.b64 %19, {a38,a39}; mov.b64 %20, {a40,a41}; mov.b64 %21, {a42,a43}; mov.b64 %22, {a44,a45}; mov.b64 %23, {a46,a47};\n}"
       : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[2][4]), "=l"(d[2][5]), "=l"(d[2][6]), "=l"(d[2][7])
-      : "r"(t), "r"(t + 1 * OZ_BN), "r"(t + 2 * OZ_BN)
+      : "r"(t), "r"(t + 1 * stride), "r"(t + 2 * stride)
       : "memory");
 }
 template <>
-__device__ __forceinline__ void tmem_ld16_pairs<4>(uint32_t t, uint64_t (&d)[4][8]) {
+__device__ __forceinline__ void tmem_ld16_pairs<4>(uint32_t t, uint32_t stride, uint64_t (&d)[4][8]) {
   asm volatile(
       "{\n.reg .b32 a<64>;\n"
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, [%32];\n"
@@ -161,31 +173,36 @@ __device__ __forceinline__ void tmem_ld16_pairs<4>(uint32_t t, uint64_t (&d)[4][
       "tcgen05.wait::ld.sync.aligned;\n"
       "mov.b64 %0, {a0,a1}; mov.b64 %1, {a2,a3}; mov.b64 %2, {a4,a5}; mov.b64 %3, {a6,a7}; mov.b64 %4, {a8,a9}; mov.b64 %5, {a10,a11}; mov.b64 %6, {a12,a13}; mov.b64 %7, {a14,a15}; mov.b64 %8, {a16,a17}; mov.b64 %9, {a18,a19}; mov.b64 %10, {a20,a21}; mov.b64 %11, {a22,a23}; mov.b64 %12, {a24,a25}; mov.b64 %13, {a26,a27}; mov.b64 %14, {a28,a29}; mov.b64 %15, {a30,a31}; mov.b64 %16, {a32,a33}; mov.b64 %17, {a34,a35}; mov.b64 %18, {a36,a37}; mov.b64 %19, {a38,a39}; mov.b64 %20, {a40,a41}; mov.b64 %21, {a42,a43}; mov.b64 %22, {a44,a45}; mov.b64 %23, {a46,a47}; mov.b64 %24, {a48,a49}; mov.b64 %25, {a50,a51}; mov.b64 %26, {a52,a53}; mov.b64 %27, {a54,a55}; mov.b64 %28, {a56,a57}; mov.b64 %29, {a58,a59}; mov.b64 %30, {a60,a61}; mov.b64 %31, {a62,a63};\n}"
       : "=l"(d[0][0]), "=l"(d[0][1]), "=l"(d[0][2]), "=l"(d[0][3]), "=l"(d[0][4]), "=l"(d[0][5]), "=l"(d[0][6]), "=l"(d[0][7]), "=l"(d[1][0]), "=l"(d[1][1]), "=l"(d[1][2]), "=l"(d[1][3]), "=l"(d[1][4]), "=l"(d[1][5]), "=l"(d[1][6]), "=l"(d[1][7]), "=l"(d[2][0]), "=l"(d[2][1]), "=l"(d[2][2]), "=l"(d[2][3]), "=l"(d[2][4]), "=l"(d[2][5]), "=l"(d[2][6]), "=l"(d[2][7]), "=l"(d[3][0]), "=l"(d[3][1]), "=l"(d[3][2]), "=l"(d[3][3]), "=l"(d[3][4]), "=l"(d[3][5]), "=l"(d[3][6]), "=l"(d[3][7])
-      : "r"(t), "r"(t + 1 * OZ_BN), "r"(t + 2 * OZ_BN), "r"(t + 3 * OZ_BN)
+      : "r"(t), "r"(t + 1 * stride), "r"(t + 2 * stride), "r"(t + 3 * stride)
       : "memory");
 }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Tile t of the launch (slots outermost): its slot, origin and K range in 32-wide stages.
+// Lower launches enumerate row-major the tiles that reach the diagonal or below: with R = 128 / BN
+// tiles per 128 columns, tile row u holds R (u + 1) of them and starts at R u (u + 1) / 2.
 struct OzTile {
   int slot, m0, n0, k_lo, n_st;
 };
+template <int BN>
 __device__ __forceinline__ OzTile oz_tile(const OzArgs& p, int t) {
+  constexpr int R = OZ_BM / BN;
   OzTile r;
   r.slot = t / p.tiles_per_slot;
   const int x = t - r.slot * p.tiles_per_slot;
   int tm, tn;
   if (p.lower) {
-    int u = (int)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);  // corrected below (no FP64 on this GPU's hot path)
-    while (u * (u + 1) / 2 > x) --u;
-    while ((u + 1) * (u + 2) / 2 <= x) ++u;
+    const int xr = x / R;  // R u (u + 1) / 2 <= x  <=>  u (u + 1) / 2 <= floor(x / R)
+    int u = (int)((sqrtf(8.0f * (float)xr + 1.0f) - 1.0f) * 0.5f);  // corrected below (no FP64 on this GPU's hot path)
+    while (u * (u + 1) / 2 > xr) --u;
+    while ((u + 1) * (u + 2) / 2 <= xr) ++u;
     tm = u;
-    tn = x - u * (u + 1) / 2;
+    tn = x - R * (u * (u + 1) / 2);
   } else {
     tm = x / p.tiles_n;
     tn = x - tm * p.tiles_n;
   }
   r.m0 = tm * OZ_BM;
-  r.n0 = tn * OZ_BN;
+  r.n0 = tn * BN;
   int k_lo = 0;
   if (p.k_mode == 1) k_lo = max(r.m0, r.n0);
   else if (p.k_mode == 2) k_lo = r.n0;
@@ -198,17 +215,17 @@ __device__ __forceinline__ OzTile oz_tile(const OzArgs& p, int t) {
 
 }  // namespace
 
-template <int S>
+template <int S, int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzArgs p) {
-  using Cfg = OzCfg<S>;
-  constexpr int NST = Cfg::NST, NACC = Cfg::NACC;
+  using Cfg = OzCfg<S, BN>;
+  constexpr int NST = Cfg::NST, NACC = Cfg::NACC, NBUF = Cfg::NBUF, CPT = Cfg::CPT;
   constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float2* staging = reinterpret_cast<float2*>(smem + NST * STAGE_BYTES);
   float* colsc_all = reinterpret_cast<float*>(smem + NST * STAGE_BYTES + OZ_STAGING_BYTES);
-  __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full, acc_empty, done_bar;
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full[NBUF], acc_empty[NBUF], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh_;
   volatile int& abort_sh = abort_sh_;
@@ -219,8 +236,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, OZ_EPI_WARPS * 32);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], OZ_EPI_WARPS * 32);
+    }
     mbar_init(&done_bar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -243,7 +262,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       int g = 0;  // stages issued by this CTA
       for (int t = blockIdx.x; t < p.tiles_total && !abort_sh; t += gridDim.x) {
-        const OzTile ti = oz_tile(p, t);
+        const OzTile ti = oz_tile<BN>(p, t);
         for (int s = 0; s < ti.n_st; ++s, ++g) {
           const int st = g % NST, u = g / NST;
           if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1, lim)) {
@@ -254,7 +273,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int k = ti.k_lo + s * OZ_KS;
           mbar_expect_tx(&full[st], STAGE_BYTES);
           tma_load_3d(dst, &tmA, k, ti.m0, ti.slot * S, &full[st]);
-          tma_load_3d(dst + S * OZ_SLICE_BYTES, &tmB, k, ti.n0, ti.slot * S, &full[st]);
+          tma_load_3d(dst + S * Cfg::A_SLICE, &tmB, k, ti.n0, ti.slot * S, &full[st]);
         }
       }
       if (abort_sh) {
@@ -267,18 +286,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ------------------------------ MMA issuer ------------------------------
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_ROLE_REGS));
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                              ((uint32_t)(OZ_BM >> 4) << 24);
       int g = 0, c = 0;  // stages consumed, chunks completed
       bool ok = true;
       for (int t = blockIdx.x; t < p.tiles_total && ok && !abort_sh; t += gridDim.x) {
-        const OzTile ti = oz_tile(p, t);
+        const OzTile ti = oz_tile<BN>(p, t);
         bool first_in_chunk = true;
         for (int s = 0; s < ti.n_st; ++s, ++g) {
           const int k = ti.k_lo + s * OZ_KS;
-          if (first_in_chunk && c > 0) {
-            // the epilogue has read the previous chunk out of the accumulators
-            if (!mbar_wait(&acc_empty, (c - 1) & 1, lim)) {
+          if (first_in_chunk && c >= NBUF) {
+            // the epilogue has read the chunk that last used this accumulator set
+            if (!mbar_wait(&acc_empty[c % NBUF], (c / NBUF - 1) & 1, lim)) {
               ok = false;
               break;
             }
@@ -291,13 +310,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t set = tmem + (uint32_t)((c % NBUF) * Cfg::ACC_COLS);
 #pragma unroll
           for (int i = 0; i < S; ++i) {
 #pragma unroll
             for (int j = 0; j < S - i; ++j) {
               const int acc_idx = (i + j) < NACC ? (i + j) : NACC - 1;
-              const uint32_t d_tmem = tmem + (uint32_t)(acc_idx * OZ_BN);
-              const uint32_t a_addr = base + i * OZ_SLICE_BYTES, b_addr = base + (S + j) * OZ_SLICE_BYTES;
+              const uint32_t d_tmem = set + (uint32_t)(acc_idx * BN);
+              const uint32_t a_addr = base + i * Cfg::A_SLICE, b_addr = base + S * Cfg::A_SLICE + j * Cfg::B_SLICE;
 #pragma unroll
               for (int kk = 0; kk < OZ_KS / 16; ++kk) {
                 // the first write of accumulator a in a chunk is the pair (0, a), kk = 0
@@ -309,7 +329,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           mma_commit(&empty[st]);
           first_in_chunk = false;
           if (((k + OZ_KS) % OZ_CHUNK) == 0 || s == ti.n_st - 1) {
-            mma_commit(&acc_full);
+            mma_commit(&acc_full[c % NBUF]);
             ++c;
             first_in_chunk = true;
           }
@@ -327,16 +347,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_ROLE_REGS));
   } else {
     // ------------------------------ epilogue ------------------------------
-    // Thread = one row of the tile and 64 columns (warp half h).  Per chunk: drain the group
-    // accumulators into a double-float register tile and release the TMEM, so that the next
-    // chunk's (or tile's) MMAs start at once.  After the tile's last chunk, add the tile into C
+    // Thread = one row of the tile and CPT = BN / 2 columns (warp half h).  Per chunk: drain the
+    // group accumulators into a double-float register tile and release the TMEM, so that the
+    // next chunk's (or tile's) MMAs start at once.  After the tile's last chunk, add the tile into C
     // through a per-warp staging buffer: each store instruction writes 64-byte row segments.
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(OZ_EPI_REGS));
     const int ew = warp - 4;
     const int q = warp & 3, h = ew >> 2;
     const int row = q * 32 + lane;
     float2* stg = staging + ew * (32 * OZ_STG_LD);
-    float* colsc = colsc_all + ew * 64;
+    float* colsc = colsc_all + ew * CPT;
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
     const bool neg = p.beta < 0.f;
     const bool accumulate = p.alpha != 0.f;
@@ -344,18 +364,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     int c = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < p.tiles_total && ok; t += gridDim.x) {
-      const OzTile ti = oz_tile(p, t);
+      const OzTile ti = oz_tile<BN>(p, t);
       const int gr = ti.m0 + row;
-      const int col0 = ti.n0 + h * 64;
+      const int col0 = ti.n0 + h * CPT;
       float2* C = p.C + ti.slot * p.C_slot_stride;
-      float2 acc[64];  // the register tile: (hi, lo) of the thread's 64 columns
+      float2 acc[CPT];  // the register tile: (hi, lo) of the thread's CPT columns
       if (ti.n_st == 0) {
         if (p.alpha != 0.f) continue;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < CPT; ++j) acc[j] = make_float2(0.f, 0.f);
       } else {
         if (p.alpha != 0.f && gr < p.M)
-          for (int j = 0; j < 64; j += 16)
+          for (int j = 0; j < CPT; j += 16)
             if (col0 + j < p.N) prefetch_l2(C + (int64_t)gr * p.ldc + col0 + j);
         const int32_t* eA = p.expA + ti.slot * p.expA_slot_stride;
         const int32_t* eB = p.expB + ti.slot * p.expB_slot_stride;
@@ -363,16 +383,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int chunk = k / OZ_CHUNK;
           const int k_end = min(p.K, (chunk + 1) * OZ_CHUNK);
           // scales of this chunk: +-2^(eA - 14) for the thread's row (sign of beta); 2^eB for the
-          // warp's 64 columns in a per-warp shared array (read as broadcast pairs)
+          // warp's CPT columns in a per-warp shared array (read as broadcast pairs)
           float rs = pow2f(gr < p.M ? eA[(int64_t)chunk * p.expA_chunk_stride + gr] - 14 : 0);
           if (neg) rs = -rs;
           const uint64_t rs2 = f2pack(rs, rs);
           const int64_t eb_base = (int64_t)chunk * p.expB_chunk_stride;
           __syncwarp();
-          colsc[lane] = pow2f(col0 + lane < p.N ? eB[eb_base + col0 + lane] : 0);
-          colsc[lane + 32] = pow2f(col0 + 32 + lane < p.N ? eB[eb_base + col0 + 32 + lane] : 0);
+#pragma unroll
+          for (int jj = lane; jj < CPT; jj += 32) colsc[jj] = pow2f(col0 + jj < p.N ? eB[eb_base + col0 + jj] : 0);
           __syncwarp();
-          bool got = mbar_wait(&acc_full, c & 1, lim);
+          const int buf = c % NBUF;
+          bool got = mbar_wait(&acc_full[buf], (c / NBUF) & 1, lim);
           got = __all_sync(0xffffffffu, got);
           if (!got) {
             ok = false;
@@ -381,9 +402,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;");
           const bool first = (k == ti.k_lo);
 #pragma unroll
-          for (int blk2 = 0; blk2 < 4; ++blk2) {
+          for (int blk2 = 0; blk2 < CPT / 16; ++blk2) {
             uint64_t D[NACC][8];
-            tmem_ld16_pairs<NACC>(t_lane + (uint32_t)(h * 64 + blk2 * 16), D);
+            tmem_ld16_pairs<NACC>(t_lane + (uint32_t)(buf * Cfg::ACC_COLS + h * CPT + blk2 * 16), (uint32_t)BN, D);
             // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14 below
             // 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the fractions
             // exactly into the low word (multiples of 2^-14 below 1), and the rounded tail group
@@ -392,7 +413,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint64_t KR2 = f2pack(kRound, kRound);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-              const int j2 = blk2 * 8 + m;  // column pair (2 j2, 2 j2 + 1) of the thread's 64
+              const int j2 = blk2 * 8 + m;  // column pair (2 j2, 2 j2 + 1) of the thread's CPT
               const uint64_t d1 = D[1][m];
               const uint64_t t1 = sub2(add2(d1, KR2), KR2);
               uint64_t sv = add2(D[0][m], t1);
@@ -417,7 +438,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;");
-          mbar_arrive(&acc_empty);
+          mbar_arrive(&acc_empty[buf]);
           ++c;
           k = k_end;
         }
@@ -432,7 +453,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         crow[i] = C + (int64_t)grow[i] * p.ldc;
       }
 #pragma unroll
-      for (int blk = 0; blk < 8; ++blk) {
+      for (int blk = 0; blk < CPT / 8; ++blk) {
         __syncwarp();
 #pragma unroll
         for (int u = 0; u < 8; ++u) stg[lane * OZ_STG_LD + u] = acc[blk * 8 + u];
@@ -619,14 +640,14 @@ static int get_encode() {
   return INLA_OK;
 }
 
-int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S) {
+int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S, int box_rows) {
   INLA_TRY(get_encode());
   if ((op.ld_k % OZ_BK) != 0 || (op.K % OZ_BK) != 0 || ((uintptr_t)op.planes & 15) != 0 || S < 1 ||
-      S > OZ_MAX_S || nplanes % S)
+      S > OZ_MAX_S || nplanes % S || (box_rows != OZ_BM && box_rows != OZ_BN_NARROW))
     return INLA_E_BADARG;
   cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)op.ld_k * 2, (cuuint64_t)op.plane_stride * 2};
-  cuuint32_t box[3] = {OZ_KS, OZ_BM, (cuuint32_t)S};
+  cuuint32_t box[3] = {OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)S};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.planes, dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -647,23 +668,23 @@ static int num_sms() {
 }
 
 // Persistent launch: one CTA per SM (shared memory allows no second), tiles round-robin.
-template <int S>
+template <int S, int BN>
 static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs& a, int nslots, cudaStream_t st) {
-  constexpr int smem = OzCfg<S>::SMEM;
+  constexpr int smem = OzCfg<S, BN>::SMEM;
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_ozaki_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return INLA_E_CUDA;
     init = true;
   }
   if (a.tiles_total <= 0) return INLA_OK;
   const int grid = std::min(a.tiles_total, num_sms());
-  count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S><<<grid, OZ_THREADS, smem, st>>>(ma, mb, a);
+  count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S, BN><<<grid, OZ_THREADS, smem, st>>>(ma, mb, a);
   if (cudaPeekAtLastError() != cudaSuccess) return note_launch_error("k_ozaki_gemm launch");
   if (debug_sync_enabled()) {
     char site[200];
-    snprintf(site, sizeof(site), "ozaki S=%d M=%d N=%d K=%d kmode=%d lower=%d slots=%d", S, a.M, a.N, a.K, a.k_mode,
-             a.lower, nslots);
+    snprintf(site, sizeof(site), "ozaki S=%d BN=%d M=%d N=%d K=%d kmode=%d lower=%d slots=%d", S, BN, a.M, a.N, a.K,
+             a.k_mode, a.lower, nslots);
     return debug_check(st, site);
   }
   return INLA_OK;
@@ -680,30 +701,36 @@ struct OzStats {
 static OzStats g_stats;
 bool oz_stats_active() { return g_stats.on; }
 
-static double oz_alg_flops(const OzArgs& a, int nslots) {
+// Algorithmic flops of a launch: 2 K' per needed output element, K' the tile's k range
+// (lower launches need the elements on or below the diagonal).
+static double oz_alg_flops(const OzArgs& a, int nslots, int bn) {
   double f = 0.0;
-  const int tiles = a.lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
-  for (int x = 0; x < tiles; ++x) {
-    int tm, tn;
-    if (a.lower) {
-      int t = 0;
-      while ((t + 1) * (t + 2) / 2 <= x) ++t;
-      tm = t;
-      tn = x - t * (t + 1) / 2;
-    } else {
-      tm = x / a.tiles_n;
-      tn = x % a.tiles_n;
+  for (int tm = 0; tm < a.tiles_m; ++tm) {
+    const int tn_end = a.lower ? std::min(a.tiles_n, (tm + 1) * (OZ_BM / bn)) : a.tiles_n;
+    for (int tn = 0; tn < tn_end; ++tn) {
+      const int m0 = tm * OZ_BM, n0 = tn * bn;
+      int k_lo = a.k_mode == 1 ? std::max(m0, n0) : a.k_mode == 2 ? n0 : a.k_mode == 3 ? m0 : 0;
+      k_lo = (k_lo / OZ_BK) * OZ_BK;
+      if (k_lo >= a.K) continue;
+      const int rows = std::min(OZ_BM, a.M - m0), cols = std::min(bn, a.N - n0);
+      double elems = 0.0;
+      if (a.lower)
+        for (int r = m0; r < m0 + rows; ++r) elems += std::max(0, std::min(r, n0 + cols - 1) - n0 + 1);
+      else
+        elems = (double)rows * cols;
+      f += 2.0 * elems * (a.K - k_lo);
     }
-    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-    int k_lo = a.k_mode == 1 ? std::max(m0, n0) : a.k_mode == 2 ? n0 : a.k_mode == 3 ? m0 : 0;
-    k_lo = (k_lo / OZ_BK) * OZ_BK;
-    const double rows = std::min(OZ_BM, a.M - m0), cols = std::min(OZ_BN, a.N - n0);
-    double elems = rows * cols;
-    if (a.lower && tm == tn) elems = rows * (rows + 1) / 2;
-    if (k_lo < a.K) f += 2.0 * elems * (a.K - k_lo);
   }
   return f * nslots;
 }
+
+// Tile width.  The narrow (double-buffered) tile serves products of at most 64 columns, where
+// the wide tile would spend half its tensor and epilogue work on padding, and products with
+// K <= 64, where a tile is one short chunk and the wide tile's MMAs wait for every drain
+// (measured on 147456-row panels of the blocked Cholesky: 1.8x at N = 64, 1.2-1.5x at
+// N = 192..448).  Longer K stays on the wide tile: the narrow one loads A twice per 128
+// columns and measured ~30% slower there.  A test hook may force one width.
+static int g_force_bn = 0;
 
 int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int nslots, cudaStream_t st) {
   OzArgs a = args_in;
@@ -716,13 +743,14 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
   a.expB_chunk_stride = B.exp_chunk_stride;
   a.expA_slot_stride = A.exp_slot_stride;
   a.expB_slot_stride = B.exp_slot_stride;
+  const int bn = g_force_bn ? g_force_bn : (a.N <= OZ_BN_NARROW || a.K <= OZ_BK ? OZ_BN_NARROW : OZ_BN);
   a.tiles_m = (a.M + OZ_BM - 1) / OZ_BM;
-  a.tiles_n = (a.N + OZ_BN - 1) / OZ_BN;
-  a.tiles_per_slot = a.lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  a.tiles_n = (a.N + bn - 1) / bn;
+  a.tiles_per_slot = a.lower ? (OZ_BM / bn) * (a.tiles_m * (a.tiles_m + 1) / 2) : a.tiles_m * a.tiles_n;
   a.tiles_total = a.tiles_per_slot * nslots;
   CUtensorMap ma, mb;
-  INLA_TRY(oz_make_map(&ma, A, a.S * nslots, a.S));
-  INLA_TRY(oz_make_map(&mb, B, a.S * nslots, a.S));
+  INLA_TRY(oz_make_map(&ma, A, a.S * nslots, a.S, OZ_BM));
+  INLA_TRY(oz_make_map(&mb, B, a.S * nslots, a.S, bn));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (g_stats.on) {
     cudaEventCreate(&e0);
@@ -730,18 +758,19 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
     cudaEventRecord(e0, st);
   }
   int rc;
+  const bool narrow = bn == OZ_BN_NARROW;
   switch (a.S) {
-    case 2: rc = launch_oz<2>(ma, mb, a, nslots, st); break;
-    case 3: rc = launch_oz<3>(ma, mb, a, nslots, st); break;
-    case 4: rc = launch_oz<4>(ma, mb, a, nslots, st); break;
-    case 5: rc = launch_oz<5>(ma, mb, a, nslots, st); break;
+    case 2: rc = narrow ? launch_oz<2, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<2, OZ_BN>(ma, mb, a, nslots, st); break;
+    case 3: rc = narrow ? launch_oz<3, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<3, OZ_BN>(ma, mb, a, nslots, st); break;
+    case 4: rc = narrow ? launch_oz<4, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<4, OZ_BN>(ma, mb, a, nslots, st); break;
+    case 5: rc = narrow ? launch_oz<5, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<5, OZ_BN>(ma, mb, a, nslots, st); break;
     default: rc = INLA_E_BADARG;
   }
   if (g_stats.on) {
     cudaEventRecord(e1, st);
     g_stats.ev.push_back({e0, e1});
     g_stats.launches += 1;
-    const double f = oz_alg_flops(a, nslots);
+    const double f = oz_alg_flops(a, nslots, bn);
     g_stats.alg_flops += f;
     g_stats.tensor_flops += f * a.S * (a.S + 1) / 2;
   }
@@ -750,7 +779,13 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
 
 }  // namespace inla
 
-// test hooks: launch statistics of the Ozaki GEMM
+// test hooks: launch statistics of the Ozaki GEMM; forced tile width (0: by shape, 64, 128)
+extern "C" int inla_test_gemm_tile_width(int bn) {
+  using namespace inla;
+  if (bn != 0 && bn != OZ_BN && bn != OZ_BN_NARROW) return INLA_E_BADARG;
+  g_force_bn = bn;
+  return INLA_OK;
+}
 extern "C" void inla_test_stats_enable(int on) {
   using namespace inla;
   g_stats.on = on != 0;

@@ -16,12 +16,14 @@
 namespace inla {
 
 constexpr int OZ_BM = 128;      // tile rows (tcgen05 M)
-constexpr int OZ_BN = 128;      // tile columns (tcgen05 N)
+constexpr int OZ_BN = 128;      // tile columns (tcgen05 N) of the wide tile
+constexpr int OZ_BN_NARROW = 64;  // tile columns of the narrow tile (N <= 64 or K <= 64): its
+                                  // accumulator sets fit twice in the TMEM (double buffering)
 constexpr int OZ_BK = 64;       // K granularity of operands and of the k ranges
 constexpr int OZ_KS = 32;       // K per pipeline stage (64-byte swizzled rows of BF16)
 constexpr int OZ_CHUNK = 256;   // K per exact accumulation chunk (one exponent per row)
 constexpr int OZ_MAX_S = 5;
-constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_KS * 2;   // one slice of one operand for one stage
+constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_KS * 2;   // one slice of A (128 rows) for one stage
 constexpr int OZ_EPI_WARPS = 8;                     // epilogue warps (two per TMEM lane quarter)
 constexpr int OZ_THREADS = 384;                     // warpgroup 0: TMA + MMA; 1-2: epilogue
 // Register split: launched at 168 per thread (384 x 168 <= 64K; three warps share each
@@ -78,9 +80,9 @@ struct OzArgs {
   int32_t* err;      // device flag: set to nonzero on a timed-out wait
 };
 
-// Host: encode a 3-D tensor map over an operand's planes (box OZ_KS x 128 x S: all S slices
-// of 128 rows for one pipeline stage).
-int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S);
+// Host: encode a 3-D tensor map over an operand's planes (box OZ_KS x box_rows x S: all S
+// slices of box_rows rows for one pipeline stage; box_rows = 128, or 64 for a narrow B).
+int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S, int box_rows);
 // Host: C = alpha C + beta A B^T for `nslots` slots (grid.z), S slices.
 int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args, int nslots, cudaStream_t st);
 

@@ -87,3 +87,64 @@ def test_transposed_operands_lower_and_k_ranges(lib):
     got = _run(lib, Z, W, np.zeros((192, n)), 192, n, n, 4, ta=1, tb=1, kmode=2)
     ref = Z.T @ W
     assert np.all(np.abs(got - ref) <= _bound(Z.T, W.T, 4, n))
+
+
+@pytest.fixture
+def narrow(lib):
+    """Every launch on the double-buffered 128 x 64 tile (reset to the shape rule after)."""
+    assert lib.inla_test_gemm_tile_width(64) == 0
+    yield lib
+    assert lib.inla_test_gemm_tile_width(0) == 0
+
+
+@pytest.mark.parametrize("S", [2, 3, 4, 5])
+def test_narrow_tile_plain_and_accumulate(narrow, S):
+    rng = np.random.default_rng(40 + S)
+    M, N, K = 300, 200, 576          # ragged in M and N (N = 3 tiles of 64 + 8), K = 2 chunks + 64
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    Bm = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, (N, 1)))
+    C0 = rng.standard_normal((M, N))
+    got = _run(narrow, A, Bm, C0, M, N, K, S)
+    ref = A @ Bm.T
+    assert np.all(np.abs(got - ref) <= _bound(A, Bm, S, K))
+    got = _run(narrow, A, Bm, C0, M, N, K, S, alpha=1.0, beta=-1.0)
+    ref = C0 - A @ Bm.T
+    assert np.all(np.abs(got - ref) <= _bound(A, Bm, S, K) + 1e-13 * np.abs(C0))
+
+
+@pytest.mark.parametrize("n", [384, 320])
+def test_narrow_tile_lower_and_k_ranges(narrow, n):
+    """Lower launches enumerate two 64-wide tiles per 128 rows of the diagonal band; n = 320
+    leaves a tile row whose second diagonal tile lies wholly beyond the matrix."""
+    rng = np.random.default_rng(n)
+    W = np.tril(rng.standard_normal((n, n)))
+    C0 = rng.standard_normal((n, n))
+    got = _run(narrow, W, W, C0, n, n, n, 4, ta=1, tb=1, lower=1, kmode=1)
+    ref = W.T @ W
+    il = np.tril_indices(n)
+    assert np.all(np.abs(got - ref)[il] <= _bound(W.T, W.T, 4, n)[il])
+    Z = rng.standard_normal((n, 96))
+    got = _run(narrow, Z, W, np.zeros((96, n)), 96, n, n, 4, ta=1, tb=1, kmode=2)
+    assert np.all(np.abs(got - Z.T @ W) <= _bound(Z.T, W.T, 4, n))
+    got = _run(narrow, W, Z, np.zeros((n, 96)), n, 96, n, 5, ta=1, tb=1, kmode=3)
+    assert np.all(np.abs(got - W.T @ Z) <= _bound(W.T, Z.T, 5, n))
+
+
+def test_narrow_and_wide_tiles_agree_bitwise(lib):
+    """The tile width changes which CTA computes an element and how many columns one MMA
+    covers, not the element's chunk sums, their combination or its accumulation into C (N = 48
+    selects the narrow tile by shape): the two agree far below the slice truncation."""
+    rng = np.random.default_rng(77)
+    M, N, K = 520, 48, 704
+    A = rng.standard_normal((M, K))
+    Bm = rng.standard_normal((N, K))
+    C0 = rng.standard_normal((M, N))
+    auto = _run(lib, A, Bm, C0, M, N, K, 4, alpha=1.0, beta=-1.0)
+    assert lib.inla_test_gemm_tile_width(128) == 0
+    try:
+        wide = _run(lib, A, Bm, C0, M, N, K, 4, alpha=1.0, beta=-1.0)
+    finally:
+        assert lib.inla_test_gemm_tile_width(0) == 0
+    scale = np.abs(C0) + np.abs(A) @ np.abs(Bm).T
+    assert np.max(np.abs(auto - wide) / scale) < 1e-12
+    assert lib.inla_test_gemm_tile_width(96) != 0
