@@ -15,7 +15,7 @@ extern "C" {
 #endif
 
 /* C = alpha C + beta op(A) op(B)^T with the Ozaki-split tensor-core GEMM (S BF16 slices per
- * operand, exact FP32 accumulation per 256-wide K chunk, double-float C).
+ * operand, exact FP32 accumulation per 512-wide K chunk, double-float C).
  * A: row-major M x K (trans_a = 0) or K x M (trans_a = 1); B: N x K or K x N; C: M x N,
  * all host FP64 arrays.  K must be a multiple of 64.  lower = 1 computes only the lower
  * triangle (M == N); k_mode restricts K per 128 x 128 tile (0: all; 1: k >= max(row0, col0);

@@ -2,7 +2,8 @@
 // non-trivial K runs on the Ozaki-split tensor-core GEMM; the 64 x 64 diagonal tiles are
 // factored and inverted in double-float.  Two-level blocking: outer panels of NB columns (the
 // trailing updates' K; C traffic n^3 / (3 NB) element updates per factorisation; NB tuned per
-// matrix size for the Cholesky), 64-wide inner steps.
+// matrix size for the Cholesky); inside a Cholesky panel, recursive halving down to 64-wide
+// tile columns; 64-wide inner steps in the triangular solves.
 #include <map>
 #include "df64.cuh"
 #include "mixed.h"
@@ -62,36 +63,47 @@ OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, in
 
 }  // namespace
 
+// Columns [c0, c1) of an outer panel, every slot: rows >= c0 hold A minus the updates of the
+// columns left of c0.  64 wide: factor the diagonal tile in double-float and form the tile
+// column below it as X = A_panel Linv^T.  Wider: factor the left half recursively, update the
+// right half with one product of K = the left half's width, factor the right half.  The
+// within-panel updates are then a few long-K products (K = 256, 128, 64 for a 512-wide panel)
+// rather than one K = 64 update per tile column.
+static int mixed_panel(Batch& B, const MRef& M, int c0, int c1) {
+  const int n = M.n, S = B.S;
+  if (c1 - c0 <= IB) {
+    launch_potrf_diag_df(B.d_slots, B.n, M.sel, c0 / IB, B.st);
+    const int R = n - c0 - IB;
+    if (R <= 0) return INLA_OK;
+    float2* panel = M.base + (int64_t)(c0 + IB) * M.ld + c0;
+    OzOperand pa = operand(B.PA, B.EA, R, IB);
+    OzOperand pb = operand(B.PB, B.EB, IB, IB);
+    oz_slice_df(M.base, M.stride, M.ld, c0 + IB, c0, R, IB, false, pa, S, B.n, B.st);
+    oz_slice_df(reinterpret_cast<float2*>(M.linv) + (int64_t)(c0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB,
+                false, pb, S, B.n, B.st);
+    OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
+    return oz_gemm(pa, pb, a, B.n, B.st);
+  }
+  const int mid = c0 + (c1 - c0) / (2 * IB) * IB;
+  INLA_TRY(mixed_panel(B, M, c0, mid));
+  // A[mid:, mid:c1] -= L[mid:, c0:mid] L[mid:c1, c0:mid]^T  (B operand: the first w rows of A's)
+  const int R = n - mid, K = mid - c0, w = c1 - mid;
+  OzOperand px = operand(B.PA, B.EA, R, K);
+  oz_slice_df(M.base, M.stride, M.ld, mid, c0, R, K, false, px, S, B.n, B.st);
+  OzOperand pxt = px;
+  pxt.rows = w;
+  OzArgs u = gemm_args(B, M.base + (int64_t)mid * M.ld + mid, M.stride, M.ld, R, w, K, 1.f, -1.f);
+  INLA_TRY(oz_gemm(px, pxt, u, B.n, B.st));
+  return mixed_panel(B, M, mid, c1);
+}
+
 // In-place Cholesky of the matrix selected by `sel` (lower triangle), every slot: the launches.
 static int mixed_potrf_launches(Batch& B, int sel, int nb) {
   const MRef M = mref(B, sel);
   const int n = M.n, S = B.S;
   for (int K0 = 0; K0 < n; K0 += nb) {
     const int kend = std::min(K0 + nb, n);
-    for (int j0 = K0; j0 < kend; j0 += IB) {
-      launch_potrf_diag_df(B.d_slots, B.n, sel, j0 / IB, B.st);
-      const int R = n - j0 - IB;
-      if (R <= 0) continue;
-      float2* panel = M.base + (int64_t)(j0 + IB) * M.ld + j0;
-      // X = A_panel Linv^T
-      OzOperand pa = operand(B.PA, B.EA, R, IB);
-      OzOperand pb = operand(B.PB, B.EB, IB, IB);
-      oz_slice_df(M.base, M.stride, M.ld, j0 + IB, j0, R, IB, false, pa, S, B.n, B.st);
-      oz_slice_df(reinterpret_cast<float2*>(M.linv) + (int64_t)(j0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB,
-                  false, pb, S, B.n, B.st);
-      OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
-      INLA_TRY(oz_gemm(pa, pb, a, B.n, B.st));
-      // rest of the 256-wide panel: A[j0+64:, j0+64:kend] -= X X_top^T
-      const int w = kend - (j0 + IB);
-      if (w > 0) {
-        OzOperand px = operand(B.PA, B.EA, R, IB);
-        oz_slice_df(M.base, M.stride, M.ld, j0 + IB, j0, R, IB, false, px, S, B.n, B.st);
-        OzOperand pxt = px;
-        pxt.rows = w;  // the first w rows of X, same planes
-        OzArgs u = gemm_args(B, M.base + (int64_t)(j0 + IB) * M.ld + (j0 + IB), M.stride, M.ld, R, w, IB, 1.f, -1.f);
-        INLA_TRY(oz_gemm(px, pxt, u, B.n, B.st));
-      }
-    }
+    INLA_TRY(mixed_panel(B, M, K0, kend));
     const int R2 = n - kend;
     if (R2 > 0) {
       OzOperand pp = operand(B.PA, B.EA, R2, kend - K0);

@@ -9,7 +9,7 @@
 //               BF16 x BF16 -> FP32) into min(S, 4) accumulators, slice-order d = i + j
 //               (groups d >= 3 share the last one); with BN = 64 two accumulator sets
 //               alternate by chunk, so the MMAs run on while the epilogue reads the other set;
-//   warps 4..11 epilogue: after each 256-wide K chunk, read the accumulators (tcgen05.ld),
+//   warps 4..11 epilogue: after each 512-wide K chunk, read the accumulators (tcgen05.ld),
 //               combine them in double-float, scale by 2^(eA + eB - 14) and add the chunk
 //               into a register tile, then release the TMEM so that the next chunk (or tile)
 //               runs on the tensor cores while the finished tile is added into C (double-float,
@@ -405,11 +405,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int blk2 = 0; blk2 < CPT / 16; ++blk2) {
             uint64_t D[NACC][8];
             tmem_ld16_pairs<NACC>(t_lane + (uint32_t)(buf * Cfg::ACC_COLS + h * CPT + blk2 * 16), (uint32_t)BN, D);
-            // Group 0 holds integers below 2^22, groups 1 and 2 multiples of 2^-7 and 2^-14 below
-            // 2^16 and 2^10: the integer parts add exactly in FP32 (below 2^24), the fractions
-            // exactly into the low word (multiples of 2^-14 below 1), and the rounded tail group
-            // (d >= 3) costs ~2^-24 of a value below 2^4.  Integer parts by the 1.5 * 2^23 shift
-            // (exact for |x| < 2^22); two columns per f32x2 instruction.
+            // Group 0 holds integers of magnitude <= 2^23, groups 1 and 2 multiples of 2^-7 and
+            // 2^-14 of magnitude <= 2^16 and 640: the integer parts add exactly in FP32 (below
+            // 2^24), the fractions exactly into the low word (multiples of 2^-14 below 1), and the
+            // rounded tail group (d >= 3) costs ~2^-24 of a value below 2^3.  Integer parts by the
+            // 1.5 * 2^23 shift (exact for |x| < 2^22); two columns per f32x2 instruction.
             const uint64_t KR2 = f2pack(kRound, kRound);
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------------
-// slicing: per (row, 256-chunk) power-of-two scale and S slices of 7 bits
+// slicing: per (row, 512-chunk) power-of-two scale and S slices of 7 bits
 // ------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ df load_df(const T* p);
@@ -552,9 +552,10 @@ __device__ __forceinline__ int chunk_exponent(float m) {
   return e;
 }
 
-// Untransposed source: a group of G lanes (8, 16 or 32: the chunk width / 8) per (operand
-// row, chunk); lane g of the group covers k = chunk * 256 + 8g .. +7.
-template <typename T, int G>
+// Untransposed source: a group of G lanes (8, 16 or 32) per (operand row, chunk); lane g of the
+// group covers the NSEG segments k = chunk * OZ_CHUNK + 8 (G seg + g) .. +7 (G * 8 * NSEG is
+// the chunk width, or K when K is shorter).
+template <typename T, int G, int NSEG>
 __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
                                                     int R, int K, OzOperand dst, int S) {
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
@@ -564,14 +565,19 @@ __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_sl
   const int r = active ? (int)(grp / nchunks) : 0, ch = active ? (int)(grp % nchunks) : 0;
   const int slot = blockIdx.y;
   const T* s = src + slot * src_slot_stride + (int64_t)(row0 + r) * ld + col0;
-  const int k0 = ch * OZ_CHUNK + gl * 8;
-  const bool valid = active && k0 < K;
-  df x[8];
+  df x[NSEG][8];
+  int k0[NSEG];
+  bool valid[NSEG];
   float mx = 0.f;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    x[i] = valid ? load_df<T>(s + k0 + i) : df_make(0.f, 0.f);
-    mx = fmaxf(mx, fabsf(x[i].hi));
+  for (int g = 0; g < NSEG; ++g) {
+    k0[g] = ch * OZ_CHUNK + (g * G + gl) * 8;
+    valid[g] = active && k0[g] < K;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[g][i] = valid[g] ? load_df<T>(s + k0[g] + i) : df_make(0.f, 0.f);
+      mx = fmaxf(mx, fabsf(x[g][i].hi));
+    }
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -579,48 +585,73 @@ __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_sl
   const int e = chunk_exponent(mx * (1.0f + 1.2e-7f));
   if (active && gl == 0) dst.exps[slot * dst.exp_slot_stride + (int64_t)ch * dst.exp_chunk_stride + r] = e;
   uint16_t* planes = dst.planes + (int64_t)slot * S * dst.plane_stride;
-  slice_and_store(x, e, planes, dst.plane_stride, S, (int64_t)r * dst.ld_k + k0, valid);
+#pragma unroll
+  for (int g = 0; g < NSEG; ++g)
+    slice_and_store(x[g], e, planes, dst.plane_stride, S, (int64_t)r * dst.ld_k + k0[g], valid[g]);
 }
 
-// Transposed source: a block handles 16 operand rows x one 256-chunk through shared memory.
-// The tile is stored row-major by operand row with the k index swizzled (k ^ ((k >> 3) & 15)),
-// so that both the transposing writes (16 rows, one k) and the per-lane reads (one row, k =
-// 8 lane + i) are free of bank conflicts.
+// Transposed source: a block handles 16 operand rows x one chunk through shared memory
+// (dynamic: 16 x (OZ_CHUNK + 1) double-float cells).  The tile is stored row-major by operand
+// row with the k index swizzled (k ^ ((k >> 3) & 15)), so that both the transposing writes
+// (16 rows, one k) and the per-lane reads (one row, k = 8 lane + i + 256 g) are free of bank
+// conflicts.  Only the chunk's part below K is loaded.
+constexpr int SLICE_COLS_LDT = OZ_CHUNK + 1;  // odd row stride (float2): the 16 rows of a write hit distinct banks
+constexpr int SLICE_COLS_SMEM = 16 * SLICE_COLS_LDT * 8;
 template <typename T>
 __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
                                                     int R, int K, OzOperand dst, int S) {
-  constexpr int LDT = OZ_CHUNK + 1;  // odd row stride (float2): the 16 rows of a write hit distinct banks
-  __shared__ float2 tile[16 * LDT];
+  constexpr int LDT = SLICE_COLS_LDT, NSEG = OZ_CHUNK / 256;
+  extern __shared__ float2 tile[];
   const int r0 = blockIdx.x * 16, ch = blockIdx.z, slot = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kk_end = min(OZ_CHUNK, K - ch * OZ_CHUNK);
   const T* s = src + slot * src_slot_stride;
-  for (int kk = warp * 2 + (lane >> 4); kk < OZ_CHUNK; kk += 16) {
-    const int k = ch * OZ_CHUNK + kk, r = r0 + (lane & 15);
-    df v = df_make(0.f, 0.f);
-    if (k < K && r < R) v = load_df<T>(s + (int64_t)(row0 + k) * ld + col0 + r);
-    tile[(lane & 15) * LDT + (kk ^ ((kk >> 3) & 15))] = make_float2(v.hi, v.lo);
+  const int r = r0 + (lane & 15);
+  // eight loads in flight per thread before their shared-memory stores
+  for (int kb = warp * 2 + (lane >> 4); kb < kk_end; kb += 16 * 8) {
+    df v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int kk = kb + 16 * u;
+      v[u] = df_make(0.f, 0.f);
+      if (kk < kk_end && r < R) v[u] = load_df<T>(s + (int64_t)(row0 + ch * OZ_CHUNK + kk) * ld + col0 + r);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int kk = kb + 16 * u;
+      if (kk < kk_end) tile[(lane & 15) * LDT + (kk ^ ((kk >> 3) & 15))] = make_float2(v[u].hi, v[u].lo);
+    }
   }
   __syncthreads();
   for (int rr = warp * 2; rr < warp * 2 + 2; ++rr) {
-    const int r = r0 + rr;
-    if (r >= R) break;
-    const int k0 = ch * OZ_CHUNK + lane * 8;
-    const bool valid = k0 < K;
-    df x[8];
+    const int rw = r0 + rr;
+    if (rw >= R) break;
+    df x[NSEG][8];
+    int k0[NSEG];
+    bool valid[NSEG];
     float mx = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int kk = lane * 8 + i;
-      const float2 t = tile[rr * LDT + (kk ^ ((kk >> 3) & 15))];
-      x[i] = df_make(t.x, t.y);
-      mx = fmaxf(mx, fabsf(t.x));
+    for (int g = 0; g < NSEG; ++g) {
+      const int kb = g * 256 + lane * 8;
+      k0[g] = ch * OZ_CHUNK + kb;
+      valid[g] = kb < kk_end;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int kk = kb + i;
+        float2 t = make_float2(0.f, 0.f);
+        if (valid[g]) t = tile[rr * LDT + (kk ^ ((kk >> 3) & 15))];
+        x[g][i] = df_make(t.x, t.y);
+        mx = fmaxf(mx, fabsf(t.x));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = chunk_exponent(mx * (1.0f + 1.2e-7f));
-    if (lane == 0) dst.exps[slot * dst.exp_slot_stride + (int64_t)ch * dst.exp_chunk_stride + r] = e;
+    if (lane == 0) dst.exps[slot * dst.exp_slot_stride + (int64_t)ch * dst.exp_chunk_stride + rw] = e;
     uint16_t* planes = dst.planes + (int64_t)slot * S * dst.plane_stride;
-    slice_and_store(x, e, planes, dst.plane_stride, S, (int64_t)r * dst.ld_k + k0, valid);
+#pragma unroll
+    for (int g = 0; g < NSEG; ++g)
+      slice_and_store(x[g], e, planes, dst.plane_stride, S, (int64_t)rw * dst.ld_k + k0[g], valid[g]);
   }
 }
 
@@ -819,16 +850,23 @@ static void slice_impl(const T* src, int64_t sss, int ld, int row0, int col0, in
   if (R <= 0 || K <= 0) return;
   const int nchunks = (K + OZ_CHUNK - 1) / OZ_CHUNK;
   if (!transposed) {
-    // lanes per (row, chunk): the chunk width / 8 (K is a multiple of 64)
-    const int G = K >= OZ_CHUNK ? 32 : K <= 64 ? 8 : K <= 128 ? 16 : 32;
+    // lanes per (row, chunk): K / 8 up to 32 lanes (K is a multiple of 64), then 2 segments
+    static_assert(OZ_CHUNK == 512, "segment choice below");
+    const int G = K <= 64 ? 8 : K <= 128 ? 16 : 32;
     const int64_t threads = (int64_t)R * nchunks * G;
     const dim3 grid((unsigned)((threads + 255) / 256), nslots);
     count_launch("k_slice_rows<T>");
-    if (G == 8) k_slice_rows<T, 8><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
-    else if (G == 16) k_slice_rows<T, 16><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
-    else k_slice_rows<T, 32><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    if (G == 8) k_slice_rows<T, 8, 1><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    else if (G == 16) k_slice_rows<T, 16, 1><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    else if (K <= 256) k_slice_rows<T, 32, 1><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    else k_slice_rows<T, 32, 2><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   } else {
-    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_slice_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLICE_COLS_SMEM);
+      attr = true;
+    }
+    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, SLICE_COLS_SMEM, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   }
   if (debug_sync_enabled()) {
     char site[200];

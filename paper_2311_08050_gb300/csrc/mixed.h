@@ -34,10 +34,10 @@ void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st);
 
 // Outer block of the mixed blocked routines: the trailing updates have K = outer block (C is
-// read and written n^3 / (3 NB) times per factorisation).  512 (two exact 256-wide chunks summed
-// in the GEMM's registers) halves that traffic but widens the skinny K = 64 updates inside each
-// outer panel; the Cholesky picks between the candidates per matrix size (mixed_potrf's tuner),
-// the triangular solves use MIXED_NB.
+// read and written n^3 / (3 NB) times per factorisation).  512 (one exact 512-wide chunk per
+// update) halves that traffic but deepens the recursive panel factorisation inside each outer
+// panel; the Cholesky picks between the candidates per matrix size (mixed_potrf's tuner), the
+// triangular solves use MIXED_NB.
 constexpr int MIXED_NB = 256;
 constexpr int MIXED_NB_MAX = 512;   // workspace capacity (largest candidate)
 

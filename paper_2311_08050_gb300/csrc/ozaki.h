@@ -1,10 +1,13 @@
 // Ozaki-split GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA).
 //
-// Each operand row is scaled by a power of two per 256-wide K chunk and cut into S slices of
-// 7 bits (integers |v| <= 128 held exactly in BF16):  x = 2^e sum_i v_i 2^{-7(i+1)} + r,
-// |r| <= 2^{e-7S-1}.  A chunk's product is then sum_{i+j<S} 2^{-7(i+j+2)} (V_i W_j^T): every
-// slice product is an integer below 2^14, so the FP32 tensor-core sums over <= 256 terms
-// are exact (< 2^24), and the S groups d = i+j are kept in S separate TMEM accumulators.
+// Each operand row is scaled by a power of two per 512-wide K chunk and cut into S slices of
+// 7 bits (integers held exactly in BF16: |v_0| <= 128, |v_i| <= 64 for i >= 1, each later
+// digit being a rounded remainder of magnitude <= 1/2 scaled by 2^7):
+// x = 2^e sum_i v_i 2^{-7(i+1)} + r, |r| <= 2^{e-7S-1}.  A chunk's product is then
+// sum_{i+j<S} 2^{-7(i+j+2)} (V_i W_j^T), and the FP32 tensor-core sums of the groups
+// d = i + j <= 2 are exact over 512 terms: per term |v_0 w_0| <= 2^14,
+// |v_0 w_1| + |v_1 w_0| <= 2^14 and |v_0 w_2| + |v_1 w_1| + |v_2 w_0| <= 5 2^12, so every
+// partial sum is an integer (in units of its group) below 5 2^21 < 2^24.
 // The epilogue combines them in double-float (FP32 pairs) and updates a double-float C.
 // (Splitting of floating-point operands into error-free slices: Ozaki, Ogita, Oishi, Rump,
 // Numer. Algorithms 59 (2012).)
@@ -21,7 +24,7 @@ constexpr int OZ_BN_NARROW = 64;  // tile columns of the narrow tile (N <= 64 or
                                   // accumulator sets fit twice in the TMEM (double buffering)
 constexpr int OZ_BK = 64;       // K granularity of operands and of the k ranges
 constexpr int OZ_KS = 32;       // K per pipeline stage (64-byte swizzled rows of BF16)
-constexpr int OZ_CHUNK = 256;   // K per exact accumulation chunk (one exponent per row)
+constexpr int OZ_CHUNK = 512;   // K per exact accumulation chunk (one exponent per row)
 constexpr int OZ_MAX_S = 5;
 constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_KS * 2;   // one slice of A (128 rows) for one stage
 constexpr int OZ_EPI_WARPS = 8;                     // epilogue warps (two per TMEM lane quarter)
@@ -39,7 +42,7 @@ constexpr int OZ_COLSC_BYTES = OZ_EPI_WARPS * 64 * 4;  // per-warp column scale 
 constexpr int OZ_SMEM_BUDGET = 232448 - 512;        // opt-in maximum less the static barriers
 // TMEM accumulators per tile (4 x 128 columns = all 512).  Slice i is stored pre-scaled by
 // 2^(-7i), so a product V_i W_j^T arrives with its weight 2^(-7(i+j)): groups d = 0, 1, 2 are
-// exact in FP32 (integers times 2^(-7d) with < 24 significant bits over a 256-wide chunk) and
+// exact in FP32 (integers times 2^(-7d) with < 24 significant bits over a 512-wide chunk) and
 // every group d >= 3 is summed into the fourth accumulator, where FP32 rounding costs
 // ~2^-24 of a 2^-21-scaled quantity, i.e. ~2^-45 of the product: negligible against the
 // 2^-7S slice truncation.

@@ -1,6 +1,6 @@
 """The Ozaki-split tcgen05 GEMM (test hook of include/inla_testing.h) against FP64 numpy.
 
-With S slices of 7 bits per operand row (scaled per 256-wide chunk) the only errors are the
+With S slices of 7 bits per operand row (scaled per 512-wide chunk) the only errors are the
 dropped slice products i + j >= S and the slicing remainder, both below
 (S + 2) 2^-7S |A_i,:|_max |B_j,:|_max per K term, so
 |C - A B^T| <= (S + 2) 2^-7S K max|A_i,:| max|B_j,:| (plus double-float rounding, 2^-46
@@ -46,7 +46,7 @@ def _bound(A, Bm, S, K):
 @pytest.mark.parametrize("S", [2, 3, 4, 5])
 def test_plain_product_within_slice_bound(lib, S):
     rng = np.random.default_rng(S)
-    M, N, K = 300, 260, 320          # ragged tiles, K = one full chunk + a partial one
+    M, N, K = 300, 260, 576          # ragged tiles, K = one full chunk + a partial one
     A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
     Bm = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, (N, 1)))
     C0 = rng.standard_normal((M, N))
@@ -100,7 +100,7 @@ def narrow(lib):
 @pytest.mark.parametrize("S", [2, 3, 4, 5])
 def test_narrow_tile_plain_and_accumulate(narrow, S):
     rng = np.random.default_rng(40 + S)
-    M, N, K = 300, 200, 576          # ragged in M and N (N = 3 tiles of 64 + 8), K = 2 chunks + 64
+    M, N, K = 300, 200, 1088         # ragged in M and N (N = 3 tiles of 64 + 8), K = 2 chunks + 64
     A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
     Bm = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, (N, 1)))
     C0 = rng.standard_normal((M, N))
