@@ -63,7 +63,9 @@ int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
 
 /* The outer block (panel width) the mixed Cholesky chose for matrices of padded size n_pad
  * factored with `slices` slices: 256 or 512 once its two timed candidate runs are complete,
- * 0 while undecided (sizes below 1024 always use 256). */
+ * 0 while undecided (sizes below 1024 always use 256).  With the environment variable
+ * INLA_OUTER_BLOCK=256 or 512 (read once) every size uses that block, untuned (for profiler
+ * captures, whose timings would mislead the tuner), and this returns it. */
 int inla_test_outer_block(int32_t n_pad, int32_t slices);
 
 #ifdef __cplusplus

@@ -4,6 +4,7 @@
 // trailing updates' K; C traffic n^3 / (3 NB) element updates per factorisation; NB tuned per
 // matrix size for the Cholesky); inside a Cholesky panel, recursive halving down to 64-wide
 // tile columns; 64-wide inner steps in the triangular solves.
+#include <cstdlib>
 #include <map>
 #include "df64.cuh"
 #include "mixed.h"
@@ -164,9 +165,21 @@ struct NbTune {
 };
 std::map<std::pair<int, int>, NbTune> g_nb_tune;
 
+// INLA_OUTER_BLOCK=256 or 512 pins the outer block of every mixed Cholesky (no tuning runs):
+// under a profiler the tuner's timings would not reflect the unprofiled program.
+int pinned_nb() {
+  static const int v = [] {
+    const char* e = getenv("INLA_OUTER_BLOCK");
+    const int x = e ? atoi(e) : 0;
+    return (x == kNbCandidates[0] || x == kNbCandidates[1]) ? x : 0;
+  }();
+  return v;
+}
+
 int pick_nb(const MRef& M, int S, NbTune*& tune, int& cand) {
   tune = nullptr;
   cand = -1;
+  if (pinned_nb()) return pinned_nb();
   if (M.n < 2 * kNbCandidates[1]) return kNbCandidates[0];  // too small for the wider panel to matter
   NbTune& t = g_nb_tune[{M.n, S}];
   if (t.best) return t.best;
@@ -192,6 +205,7 @@ int pick_nb(const MRef& M, int S, NbTune*& tune, int& cand) {
 }  // namespace
 
 int mixed_nb_choice(int n, int S) {
+  if (pinned_nb()) return pinned_nb();
   auto it = g_nb_tune.find({n, S});
   return it == g_nb_tune.end() ? 0 : it->second.best;
 }

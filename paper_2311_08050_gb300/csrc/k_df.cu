@@ -192,12 +192,13 @@ __global__ void k_s_pad_identity(Slot* slots) {
 
 // Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
 // GPU's FP64 rate is ~2 FMA/clock/SM).  Register-blocked: thread (ty, tx) of a 16 x 16 grid
-// owns the 16 elements (ty + 16 bi, tx + 16 bc); each step broadcasts one column (factor) or
-// one row and one column (inverse) through double-buffered shared arrays, one barrier per step.
-// Factor: right-looking on the unscaled columns, a_ic -= a_ij a_cj / a_jj for j < c <= i, then
-// L_ij = a_ij / sqrt(a_jj).  Inverse: right-looking on the unscaled rows of X = L^-1,
-// Y_ic -= (L_ik / L_kk) Y_kc for c <= k < i, then X_ic = Y_ic / L_ii.  Stores the factor tile
-// (double-float, upper part zeroed) and the inverse tile (double-float, in the FP64-sized
+// owns the 16 elements (ty + 16 bi, tx + 16 bc) of the tile and of Y; each of the 64 steps
+// broadcasts one column of A and one row of Y through double-buffered shared arrays, one
+// barrier per step.  Augmented right-looking elimination on [A | Y = I]: step j subtracts
+// u_i = a_ij / a_jj times row j from every row i > j, i.e. a_ic -= u_i a_cj (j < c <= i) and
+// Y_ic -= u_i Y_jc (c <= j).  Then A = L_1 D L_1^T with L_1 = unit lower and Y = L_1^-1, so
+// L_ij = a_ij / sqrt(a_jj) and L^-1 = D^-1/2 Y: (L^-1)_ic = Y_ic / L_ii.  Stores the factor
+// tile (double-float, upper part zeroed) and the inverse tile (double-float, in the FP64-sized
 // cells of the inverse-tile array).
 __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int kt) {
   const Slot& s = slots[blockIdx.x];
@@ -217,12 +218,24 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int
       const float2 v = base[(size_t)(ty + 16 * bi) * M.ld + tx + 16 * bc];
       A[bi][bc] = df_make(v.x, v.y);
     }
+  // Y: the same row operations applied to the identity (augmented elimination), which ends as
+  // the inverse of the unit lower factor; Linv = D^-1/2 Y below.
+  df Y[4][4];
+#pragma unroll
+  for (int bi = 0; bi < 4; ++bi)
+#pragma unroll
+    for (int bc = 0; bc < 4; ++bc) Y[bi][bc] = df_make((ty + 16 * bi) == (tx + 16 * bc) ? 1.f : 0.f, 0.f);
   bool bad = false;
-  // ---- factor ----
+  // ---- factor: step j subtracts (a_ij / a_jj) row j from every row i > j of [A | Y] ----
 #pragma unroll
   for (int bj = 0; bj < 4; ++bj) {
     for (int jj = 0; jj < 16; ++jj) {
       const int j = bj * 16 + jj, buf = j & 1;
+      if (ty == jj) {
+        // row j of Y is final (no later step reaches it); its nonzeros are columns c <= j
+#pragma unroll
+        for (int bc = 0; bc <= bj; ++bc) rowb[buf][tx + 16 * bc] = make_float2(Y[bj][bc].hi, Y[bj][bc].lo);
+      }
       if (tx == jj) {
 #pragma unroll
         for (int bi = bj; bi < 4; ++bi) colb[buf][ty + 16 * bi] = make_float2(A[bi][bj].hi, A[bi][bj].lo);
@@ -248,6 +261,11 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int
           for (int bc = bj; bc <= bi; ++bc) {
             const int c = tx + 16 * bc;
             if (c > j && c <= i) A[bi][bc] = df_add_fast(A[bi][bc], df_neg(df_mul(u, df_make(colb[buf][c].x, colb[buf][c].y))));
+          }
+#pragma unroll
+          for (int bc = 0; bc <= bj; ++bc) {
+            const int c = tx + 16 * bc;
+            if (c <= j) Y[bi][bc] = df_add_fast(Y[bi][bc], df_neg(df_mul(u, df_make(rowb[buf][c].x, rowb[buf][c].y))));
           }
         }
       }
@@ -275,40 +293,6 @@ __global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int
       else if (c == i) A[bi][bc] = df_make(dsq[i].x, dsq[i].y);
       else A[bi][bc] = df_make(0.f, 0.f);
     }
-  // ---- inverse ----
-  df Y[4][4];
-#pragma unroll
-  for (int bi = 0; bi < 4; ++bi)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) Y[bi][bc] = df_make((ty + 16 * bi) == (tx + 16 * bc) ? 1.f : 0.f, 0.f);
-#pragma unroll
-  for (int bk = 0; bk < 4; ++bk) {
-    for (int kk = 0; kk < 16; ++kk) {
-      const int k = bk * 16 + kk, buf = k & 1;
-      if (ty == kk) {
-#pragma unroll
-        for (int bc = 0; bc <= bk; ++bc) rowb[buf][tx + 16 * bc] = make_float2(Y[bk][bc].hi, Y[bk][bc].lo);
-      }
-      if (tx == kk) {
-#pragma unroll
-        for (int bi = bk; bi < 4; ++bi) colb[buf][ty + 16 * bi] = make_float2(A[bi][bk].hi, A[bi][bk].lo);
-      }
-      __syncthreads();
-      const df rdk = df_make(rdq[k].x, rdq[k].y);
-#pragma unroll
-      for (int bi = bk; bi < 4; ++bi) {
-        const int i = ty + 16 * bi;
-        if (i > k) {
-          const df w = df_mul(df_make(colb[buf][i].x, colb[buf][i].y), rdk);
-#pragma unroll
-          for (int bc = 0; bc <= bk; ++bc) {
-            const int c = tx + 16 * bc;
-            if (c <= k) Y[bi][bc] = df_add_fast(Y[bi][bc], df_neg(df_mul(w, df_make(rowb[buf][c].x, rowb[buf][c].y))));
-          }
-        }
-      }
-    }
-  }
   float2* linv = reinterpret_cast<float2*>(M.Linv) + (size_t)kt * TB * TB;
 #pragma unroll
   for (int bi = 0; bi < 4; ++bi)

@@ -591,16 +591,16 @@ __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_sl
 }
 
 // Transposed source: a block handles 16 operand rows x one chunk through shared memory
-// (dynamic: 16 x (OZ_CHUNK + 1) double-float cells).  The tile is stored row-major by operand
-// row with the k index swizzled (k ^ ((k >> 3) & 15)), so that both the transposing writes
-// (16 rows, one k) and the per-lane reads (one row, k = 8 lane + i + 256 g) are free of bank
-// conflicts.  Only the chunk's part below K is loaded.
-constexpr int SLICE_COLS_LDT = OZ_CHUNK + 1;  // odd row stride (float2): the 16 rows of a write hit distinct banks
-constexpr int SLICE_COLS_SMEM = 16 * SLICE_COLS_LDT * 8;
+// (dynamic: 16 x LDT double-float cells, LDT = min(K, OZ_CHUNK) + 1, odd so that the 16 rows
+// of a write hit distinct banks).  The tile is stored row-major by operand row with the k
+// index swizzled (k ^ ((k >> 3) & 15)), so that both the transposing writes (16 rows, one k)
+// and the per-lane reads (one row, k = 8 lane + i + 256 g) are free of bank conflicts.  Only
+// the chunk's part below K is loaded.
+constexpr int SLICE_COLS_SMEM_MAX = 16 * (OZ_CHUNK + 1) * 8;
 template <typename T>
 __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
-                                                    int R, int K, OzOperand dst, int S) {
-  constexpr int LDT = SLICE_COLS_LDT, NSEG = OZ_CHUNK / 256;
+                                                    int R, int K, OzOperand dst, int S, int LDT) {
+  constexpr int NSEG = OZ_CHUNK / 256;
   extern __shared__ float2 tile[];
   const int r0 = blockIdx.x * 16, ch = blockIdx.z, slot = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -863,10 +863,12 @@ static void slice_impl(const T* src, int64_t sss, int ld, int row0, int col0, in
   } else {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_slice_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLICE_COLS_SMEM);
+      cudaFuncSetAttribute(k_slice_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLICE_COLS_SMEM_MAX);
       attr = true;
     }
-    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, SLICE_COLS_SMEM, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
+    const int ldt = std::min(K, OZ_CHUNK) + 1;
+    const size_t smem = (size_t)16 * ldt * sizeof(float2);
+    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, smem, st>>>(src, sss, ld, row0, col0, R, K, dst, S, ldt);
   }
   if (debug_sync_enabled()) {
     char site[200];
