@@ -590,40 +590,42 @@ __global__ void __launch_bounds__(256) k_slice_rows(const T* src, int64_t src_sl
     slice_and_store(x[g], e, planes, dst.plane_stride, S, (int64_t)r * dst.ld_k + k0[g], valid[g]);
 }
 
-// Transposed source: a block handles 16 operand rows x one chunk through shared memory
-// (dynamic: 16 x LDT double-float cells, LDT = min(K, OZ_CHUNK) + 1, odd so that the 16 rows
-// of a write hit distinct banks).  The tile is stored row-major by operand row with the k
-// index swizzled (k ^ ((k >> 3) & 15)), so that both the transposing writes (16 rows, one k)
-// and the per-lane reads (one row, k = 8 lane + i + 256 g) are free of bank conflicts.  Only
-// the chunk's part below K is loaded.
-constexpr int SLICE_COLS_SMEM_MAX = 16 * (OZ_CHUNK + 1) * 8;
-template <typename T>
+// Transposed source: a block handles ROWS operand rows (16, or 8 for chunks longer than 256)
+// x one chunk through shared memory (dynamic: ROWS x LDT double-float cells, LDT = min(K,
+// OZ_CHUNK) + 1, odd so that the rows of a transposing write hit distinct banks; 8 rows keep a
+// 512-wide chunk's tile at 33 KB, so that six blocks share an SM).  The tile is stored
+// row-major by operand row with the k index swizzled (k ^ ((k >> 3) & 15)), so that both the
+// transposing writes (ROWS rows, one k) and the per-lane reads (one row, k = 8 lane + i + 256 g)
+// avoid bank conflicts.  Only the chunk's part below K is loaded.
+template <typename T, int ROWS>
 __global__ void __launch_bounds__(256) k_slice_cols(const T* src, int64_t src_slot_stride, int ld, int row0, int col0,
                                                     int R, int K, OzOperand dst, int S, int LDT) {
   constexpr int NSEG = OZ_CHUNK / 256;
+  constexpr int KPW = 32 / ROWS;          // k rows per warp per load instruction
+  constexpr int RPW = ROWS / 8;           // operand rows per warp in the slicing phase
   extern __shared__ float2 tile[];
-  const int r0 = blockIdx.x * 16, ch = blockIdx.z, slot = blockIdx.y;
+  const int r0 = blockIdx.x * ROWS, ch = blockIdx.z, slot = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kk_end = min(OZ_CHUNK, K - ch * OZ_CHUNK);
   const T* s = src + slot * src_slot_stride;
-  const int r = r0 + (lane & 15);
+  const int r = r0 + (lane % ROWS);
   // eight loads in flight per thread before their shared-memory stores
-  for (int kb = warp * 2 + (lane >> 4); kb < kk_end; kb += 16 * 8) {
+  for (int kb = warp * KPW + lane / ROWS; kb < kk_end; kb += 8 * KPW * 8) {
     df v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int kk = kb + 16 * u;
+      const int kk = kb + 8 * KPW * u;
       v[u] = df_make(0.f, 0.f);
       if (kk < kk_end && r < R) v[u] = load_df<T>(s + (int64_t)(row0 + ch * OZ_CHUNK + kk) * ld + col0 + r);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int kk = kb + 16 * u;
-      if (kk < kk_end) tile[(lane & 15) * LDT + (kk ^ ((kk >> 3) & 15))] = make_float2(v[u].hi, v[u].lo);
+      const int kk = kb + 8 * KPW * u;
+      if (kk < kk_end) tile[(lane % ROWS) * LDT + (kk ^ ((kk >> 3) & 15))] = make_float2(v[u].hi, v[u].lo);
     }
   }
   __syncthreads();
-  for (int rr = warp * 2; rr < warp * 2 + 2; ++rr) {
+  for (int rr = warp * RPW; rr < warp * RPW + RPW; ++rr) {
     const int rw = r0 + rr;
     if (rw >= R) break;
     df x[NSEG][8];
@@ -861,14 +863,15 @@ static void slice_impl(const T* src, int64_t sss, int ld, int row0, int col0, in
     else if (K <= 256) k_slice_rows<T, 32, 1><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
     else k_slice_rows<T, 32, 2><<<grid, 256, 0, st>>>(src, sss, ld, row0, col0, R, K, dst, S);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_slice_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SLICE_COLS_SMEM_MAX);
-      attr = true;
-    }
+    // 16 rows per block up to 256-wide chunks (33 KB), 8 rows for the 512-wide ones (33 KB)
     const int ldt = std::min(K, OZ_CHUNK) + 1;
-    const size_t smem = (size_t)16 * ldt * sizeof(float2);
-    count_launch("k_slice_cols<T>"), k_slice_cols<T><<<dim3((R + 15) / 16, nslots, nchunks), 256, smem, st>>>(src, sss, ld, row0, col0, R, K, dst, S, ldt);
+    if (ldt <= 257) {
+      const size_t smem = (size_t)16 * ldt * sizeof(float2);
+      count_launch("k_slice_cols<T>"), k_slice_cols<T, 16><<<dim3((R + 15) / 16, nslots, nchunks), 256, smem, st>>>(src, sss, ld, row0, col0, R, K, dst, S, ldt);
+    } else {
+      const size_t smem = (size_t)8 * ldt * sizeof(float2);
+      count_launch("k_slice_cols<T>"), k_slice_cols<T, 8><<<dim3((R + 7) / 8, nslots, nchunks), 256, smem, st>>>(src, sss, ld, row0, col0, R, K, dst, S, ldt);
+    }
   }
   if (debug_sync_enabled()) {
     char site[200];
