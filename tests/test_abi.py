@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -86,3 +87,24 @@ def test_struct_layout_matches_header(tmp_path):
         assert got[(cname, "__sizeof__")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_outer_block_pin_and_tile_width_hook_without_a_gpu(libpath):
+    """INLA_OUTER_BLOCK pins the mixed Cholesky's outer block (read once per process, so each
+    case runs in a fresh interpreter); unset, nothing is decided before a factorisation ran.
+    The GEMM tile-width hook accepts 0, 64 and 128 only."""
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); "
+            "print(L.inla_test_outer_block(16384, 4), L.inla_test_outer_block(512, 5))")
+    for pin, want in (("512", "512 512"), ("256", "256 256"), ("300", "0 0"), (None, "0 0")):
+        env = {k: v for k, v in os.environ.items() if k != "INLA_OUTER_BLOCK"}
+        if pin is not None:
+            env["INLA_OUTER_BLOCK"] = pin
+        out = subprocess.run([sys.executable, "-c", code, libpath], capture_output=True, text=True, env=env)
+        assert out.returncode == 0, out.stderr
+        assert out.stdout.split() == want.split(), (pin, out.stdout)
+    L = inla.lib()
+    for bn in (0, 64, 128):
+        assert L.inla_test_gemm_tile_width(bn) == 0
+    for bn in (32, 96, 256, -1):
+        assert L.inla_test_gemm_tile_width(bn) == inla.E_BADARG
+    assert L.inla_test_gemm_tile_width(0) == 0
