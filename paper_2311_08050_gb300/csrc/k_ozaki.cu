@@ -797,6 +797,7 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
     case 3: rc = narrow ? launch_oz<3, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<3, OZ_BN>(ma, mb, a, nslots, st); break;
     case 4: rc = narrow ? launch_oz<4, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<4, OZ_BN>(ma, mb, a, nslots, st); break;
     case 5: rc = narrow ? launch_oz<5, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<5, OZ_BN>(ma, mb, a, nslots, st); break;
+    case 6: rc = narrow ? launch_oz<6, OZ_BN_NARROW>(ma, mb, a, nslots, st) : launch_oz<6, OZ_BN>(ma, mb, a, nslots, st); break;
     default: rc = INLA_E_BADARG;
   }
   if (g_stats.on) {

@@ -25,7 +25,7 @@ constexpr int OZ_BN_NARROW = 64;  // tile columns of the narrow tile (N <= 64 or
 constexpr int OZ_BK = 64;       // K granularity of operands and of the k ranges
 constexpr int OZ_KS = 32;       // K per pipeline stage (64-byte swizzled rows of BF16)
 constexpr int OZ_CHUNK = 512;   // K per exact accumulation chunk (one exponent per row)
-constexpr int OZ_MAX_S = 5;
+constexpr int OZ_MAX_S = 6;
 constexpr int OZ_SLICE_BYTES = OZ_BM * OZ_KS * 2;   // one slice of A (128 rows) for one stage
 constexpr int OZ_EPI_WARPS = 8;                     // epilogue warps (two per TMEM lane quarter)
 constexpr int OZ_THREADS = 384;                     // warpgroup 0: TMA + MMA; 1-2: epilogue

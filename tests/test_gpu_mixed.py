@@ -65,6 +65,26 @@ def test_precision_ladder_error_decreases_with_slices():
     assert errs[0] > errs[1] > errs[2] > errs[3]
 
 
+def test_six_slices_reach_fp64_accuracy():
+    """Six slices for the prior inversion and the factor at the mode (Newton steps at 4, which
+    only steer the iteration): log pi~ within 1e-10 relative of the oracle (the FP64 target),
+    below the five-slice error, on both config-1 points tried."""
+    spec, thetas = synth.config1()
+    m = inla.Model(spec)
+    for th in thetas[:2]:
+        r = O.evaluate(spec, th)
+        e = {}
+        for S in (5, 6):
+            lp, st, _, _ = inla.eval_batch([m], th[None], precision="mixed", slices=S, newton_slices=4,
+                                           want_x=False, want_var=False)
+            assert st[0] == 0
+            e[S] = abs(lp[0] - r["log_post"])
+        rel6 = e[6] / max(1.0, abs(r["log_post"]))
+        print(f"log pi~ {r['log_post']:.6f}: error 5 slices {e[5]:.3e}, 6 slices {e[6]:.3e} (rel {rel6:.2e})")
+        assert e[6] < e[5]
+        assert rel6 <= 1e-10
+
+
 def test_mixed_ragged_with_offset():
     spec = synth.spatial_poisson("ragged", 7, 299, 900, [0.1, np.log(0.15)])
     spec.offset = np.random.default_rng(1).normal(0.2, 0.3, spec.m)

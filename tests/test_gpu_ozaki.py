@@ -43,7 +43,7 @@ def _bound(A, Bm, S, K):
     return (S + 2) * 2.0 ** (-7 * S) * K * ra * rb + 1e-13 * np.abs(A) @ np.abs(Bm).T
 
 
-@pytest.mark.parametrize("S", [2, 3, 4, 5])
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 6])
 def test_plain_product_within_slice_bound(lib, S):
     rng = np.random.default_rng(S)
     M, N, K = 300, 260, 576          # ragged tiles, K = one full chunk + a partial one
@@ -97,7 +97,7 @@ def narrow(lib):
     assert lib.inla_test_gemm_tile_width(0) == 0
 
 
-@pytest.mark.parametrize("S", [2, 3, 4, 5])
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 6])
 def test_narrow_tile_plain_and_accumulate(narrow, S):
     rng = np.random.default_rng(40 + S)
     M, N, K = 300, 200, 1088         # ragged in M and N (N = 3 tiles of 64 + 8), K = 2 chunks + 64
