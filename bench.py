@@ -101,18 +101,19 @@ def _dist_env():
     return rank, world, local
 
 
-WORKLOADS = {5: "poisson_n16384_m100000_fd9", 2: "poisson_n4096_m20000_fd7", 1: "poisson_n256_m1000_5pts"}
+BENCH_WORKLOAD = "poisson_n16384_m100000_fd9"
+CAPTURE_WORKLOADS = ("poisson_n4096_m20000_fd7", "poisson_n256_m1000_5pts")
 # ncu capture of the current GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean over
 # all 5613 GEMM launches of one n = 16384 step, outer block 512 as tuned); retake after any change
 # to the kernel or the blocking
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = {5: 0.8323e9}
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = {BENCH_WORKLOAD: 0.8323e9}
 
 
-def _workload(rank, config=5):
-    """The n = 16384 workload is the benchmark; the smaller configurations exist only for
-    profiling captures (a few GB on the device)."""
+def _workload(rank, workload=BENCH_WORKLOAD):
+    """The n = 16384 workload is the benchmark; the smaller ones exist only for profiling
+    captures (a few GB on the device)."""
     from paper_2311_08050_gb300 import synth
-    spec, thetas = synth.CONFIGS[config]()
+    spec, thetas = synth.WORKLOADS[workload]()
     if rank:  # weak scaling: every rank evaluates its own FD batch (shifted centre)
         thetas = thetas + 0.01 * rank
     return spec, thetas
@@ -132,7 +133,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import inla_oracle as O
-    spec, thetas = _workload(0, args.config)
+    spec, thetas = _workload(0, args.workload)
     times = []
     t_start = time.time()
     k = 0
@@ -148,7 +149,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.config], "n": spec.n, "m": spec.m, "batch": len(thetas),
+            "data": "synthetic", "config": {"workload": args.workload, "n": spec.n, "m": spec.m, "batch": len(thetas),
                                             "parallelism": "host cores (numpy/scipy LAPACK)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "full oracle evaluation of one FD theta point per step (n=16384)"},
@@ -169,7 +170,7 @@ def run_ours(args):
     L = inla.lib()
     L.inla_test_stats_read.argtypes = [C.POINTER(C.c_double)]
     L.inla_test_launch_count.restype = C.c_int64
-    spec, thetas = _workload(rank, args.config)
+    spec, thetas = _workload(rank, args.workload)
     nb = len(thetas)
     model = inla.Model(spec)
     stream = torch.cuda.Stream()
@@ -237,7 +238,7 @@ def run_ours(args):
     alg_rate = alg / (kms / 1e3) / 1e12 if kms > 0 else None
     # DRAM bytes per GEMM launch, measured by ncu over every GEMM launch of one step of the
     # n = 16384 workload (profiles/k_ozaki_gemm_launch_traffic_n16384.md); other workloads: none
-    traffic = GEMM_TRAFFIC_BYTES_PER_LAUNCH.get(args.config)
+    traffic = GEMM_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload)
     n_pad = ((spec.n + 255) // 256) * 256
     outer_block = {f"slices{sl}": int(L.inla_test_outer_block(n_pad, sl)) for sl in (args.newton_slices, args.slices)}
     roofline = {"bound": "tensor", "kernel": "k_ozaki_gemm<S> (tcgen05 BF16 slices)",
@@ -254,7 +255,7 @@ def run_ours(args):
                     "exact fp32 accumulation + df64 storage and diagonal tiles"
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
-           "config": {"workload": WORKLOADS[args.config], "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
+           "config": {"workload": args.workload, "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
                       "precision": args.precision, "slices": args.slices,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "outer_block_tuned": outer_block,
@@ -359,8 +360,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=150.0)
-    ap.add_argument("--config", type=int, default=5, choices=[5, 2, 1],
-                    help="5: the benchmark workload; 2 / 1: smaller cases for profiling captures")
+    ap.add_argument("--workload", default=BENCH_WORKLOAD, choices=(BENCH_WORKLOAD,) + CAPTURE_WORKLOADS,
+                    help="the benchmark workload (default) or a smaller case for profiling captures")
     ap.add_argument("--gemm", default=None, help="microbenchmark the Ozaki GEMM: 'M,N,K,S[,lower[,accumulate]];...'")
     args = ap.parse_args()
     if args.gemm:

@@ -200,7 +200,7 @@ def spatial_poisson(name, seed, n_pts, m, theta_true, anisotropic=False, folded_
     return ModelSpec(name, n, "poisson", A, y, None, blocks, prior)
 
 
-def config1():
+def poisson_n256_m1000_5pts():
     """n = 256 (intercept + 255 points), m = 1000, theta = (log sigma, log rho);
     five seeded theta points around (0, log 0.2)."""
     spec = spatial_poisson("poisson_n256_m1000", SEED_BASE + 1, 255, 1000, [0.0, np.log(0.2)])
@@ -209,7 +209,7 @@ def config1():
     return spec, thetas
 
 
-def config2():
+def poisson_n4096_m20000_fd7():
     """n = 4096 (intercept + 4095 points), m = 20000, theta = (log sigma, log rho,
     log tau_iid) with the iid effect folded into the covariance diagonal; batch of
     2*3+1 central finite-difference points."""
@@ -218,7 +218,7 @@ def config2():
     return spec, _fd_batch(th)
 
 
-def config5():
+def poisson_n16384_m100000_fd9():
     """n = 16384 (intercept + 16383 points), m = 100000, theta = (log sigma, log rho_x,
     log rho_y, log tau_iid): anisotropic range + folded iid; batch of 2*4+1 FD points."""
     th = np.array([0.0, np.log(0.2), np.log(0.1), np.log(4.0)])
@@ -227,7 +227,7 @@ def config5():
     return spec, _fd_batch(th)
 
 
-def config5_theta_true():
+def poisson_n16384_theta_true():
     return np.array([0.0, np.log(0.2), np.log(0.1), np.log(4.0)])
 
 
@@ -307,7 +307,7 @@ def spacetime_age(name, seed, n_s=50, n_t=20, n_a=8, eps=1e-5):
     return ModelSpec(name, n, "poisson", A, y, offset, blocks, prior, C=C)
 
 
-def config3():
+def spacetime_n8149_m8000_fd13():
     """50 Delaunay regions x 20 years x 8 ages (n = 8149, k = 1486 constraints), theta = six
     log precisions; batch of 2*6+1 central finite-difference points."""
     spec = spacetime_age("spacetime_age_n8149_k1486", SEED_BASE + 3)
@@ -331,7 +331,7 @@ def gaussian_spatial(name, seed, n, tau=10.0, theta=(0.0, np.log(0.2))):
     return ModelSpec(name, n, "gaussian", A, y, None, [blk], prior, lik_prec=tau)
 
 
-def config4(n_models=64, sizes=(512, 1024, 2048, 4096)):
+def gaussian_64_models_n512_4096(n_models=64, sizes=(512, 1024, 2048, 4096)):
     """64 independent Gaussian LGMs with n drawn uniformly from {512, 1024, 2048, 4096};
     each evaluated at its own seeded theta."""
     rng = np.random.default_rng(SEED_BASE + 4)
@@ -346,7 +346,8 @@ def config4(n_models=64, sizes=(512, 1024, 2048, 4096)):
 def surrogate_thetas(n_points, seed=SEED_BASE + 55, spread=0.5):
     """Training design for the learned surrogate: theta ~ N(theta_true, spread^2 I)."""
     rng = np.random.default_rng(seed)
-    return config5_theta_true() + spread * rng.standard_normal((n_points, 4))
+    return poisson_n16384_theta_true() + spread * rng.standard_normal((n_points, 4))
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+WORKLOADS = {f.__name__: f for f in (poisson_n256_m1000_5pts, poisson_n4096_m20000_fd7, spacetime_n8149_m8000_fd13,
+                                      gaussian_64_models_n512_4096, poisson_n16384_m100000_fd9)}

@@ -43,8 +43,8 @@ def _check(spec, thetas, lp, st, xs, vs, v_rtol=V_RTOL, x_rtol=X_RTOL):
     return errs
 
 
-def test_mixed_config1():
-    spec, thetas = synth.config1()
+def test_mixed_poisson_n256_m1000_5pts():
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
     _check(spec, thetas, lp, st, xs, vs)
@@ -53,7 +53,7 @@ def test_mixed_config1():
 def test_precision_ladder_error_decreases_with_slices():
     """Each extra 7-bit slice should cut the log pi~ error against the oracle (2^-7 per rung
     in the truncation term); the error must fall monotonically from 2 to 5 slices."""
-    spec, thetas = synth.config1()
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     r = O.evaluate(spec, thetas[0])
     errs = []
@@ -68,8 +68,8 @@ def test_precision_ladder_error_decreases_with_slices():
 def test_six_slices_reach_fp64_accuracy():
     """Six slices for the prior inversion and the factor at the mode (Newton steps at 4, which
     only steer the iteration): log pi~ within 1e-10 relative of the oracle (the FP64 target),
-    below the five-slice error, on both config-1 points tried."""
-    spec, thetas = synth.config1()
+    below the five-slice error, on both n = 256 points tried."""
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     for th in thetas[:2]:
         r = O.evaluate(spec, th)
@@ -117,8 +117,8 @@ def test_mixed_gaussian_uneven_groups():
 
 
 @pytest.mark.slow
-def test_mixed_config2_subset():
-    spec, thetas = synth.config2()
+def test_mixed_n4096_fd_subset():
+    spec, thetas = synth.poisson_n4096_m20000_fd7()
     sub = thetas[[0, 5]]
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], sub, precision="mixed")
@@ -162,7 +162,7 @@ def test_newton_trace_refactors_early_and_reuses_near_the_mode():
     import ctypes as C
     L = inla.lib()
     L.inla_test_newton_trace.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
-    spec, thetas = synth.CONFIGS[1]()
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     model = inla.Model(spec)
     for prec in ("mixed", "fp64"):
         inla.eval_batch([model], thetas, want_x=False, want_var=False, precision=prec)
@@ -192,10 +192,10 @@ def _check_vs_fp64(lp, st, xs, vs, ref, names):
 
 
 @pytest.mark.slow
-def test_mixed_config3_full_size_against_fp64_path():
+def test_mixed_spacetime_full_size_against_fp64_path():
     """The constrained space-time model at full size (n = 8149, k = 1486 sum-to-zero
     constraints, six log precisions): two FD points, mixed against FP64 on the GPU."""
-    spec, thetas = synth.config3()
+    spec, thetas = synth.spacetime_n8149_m8000_fd13()
     sub = thetas[[0, 7]]
     m = inla.Model(spec)
     mixed = inla.eval_batch([m], sub, precision="mixed")
@@ -207,10 +207,10 @@ def test_mixed_config3_full_size_against_fp64_path():
 
 
 @pytest.mark.slow
-def test_mixed_config4_all_uneven_models_against_fp64_path():
+def test_mixed_64_uneven_models_against_fp64_path():
     """All 64 Gaussian models of uneven size (n in {512, 1024, 2048, 4096}) in one batch call,
     each at its own theta: mixed against FP64 on the GPU, model by model."""
-    specs, thetas = synth.config4()
+    specs, thetas = synth.gaussian_64_models_n512_4096()
     ms = [inla.Model(sp) for sp in specs]
     which = np.arange(len(specs), dtype=np.int32)
     mixed = inla.eval_batch(ms, thetas, model_of_theta=which, precision="mixed")

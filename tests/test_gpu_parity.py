@@ -37,8 +37,8 @@ def _check(spec, thetas, lp, st, xs, vs, ref=None, var=True, lp_rtol=LP_RTOL, x_
             assert np.max(np.abs(vs[b] / r["var"] - 1.0)) <= v_rtol, b
 
 
-def test_config1_all_thetas():
-    spec, thetas = synth.config1()
+def test_n256_all_thetas():
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], thetas)
     _check(spec, thetas, lp, st, xs, vs)
@@ -93,7 +93,7 @@ def test_uneven_gaussian_models_in_one_batch():
 
 def test_no_observations_gives_the_theta_prior():
     """m = 0: Q* = Q_p, so the Laplace approximation is exact and equals log pi(theta)."""
-    spec, _ = synth.config1()
+    spec, _ = synth.poisson_n256_m1000_5pts()
     empty = CSR(0, spec.n, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
     spec0 = ModelSpec("empty", spec.n, "poisson", empty, np.zeros(0), None, spec.blocks, spec.theta_prior)
     th = np.array([0.1, np.log(0.3)])
@@ -126,7 +126,7 @@ def test_failed_point_does_not_poison_the_batch():
 
 
 def test_eval_theta_and_marginals_entry_points():
-    spec, thetas = synth.config1()
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     lp, x, iters = inla.eval_theta(m, thetas[2])
     r = O.evaluate(spec, thetas[2])
@@ -138,12 +138,12 @@ def test_eval_theta_and_marginals_entry_points():
 
 
 def test_bad_arguments_are_rejected():
-    spec, thetas = synth.config1()
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     m = inla.Model(spec)
     with pytest.raises(inla.InlaError) as e:
         inla.eval_batch([m], np.array([[np.nan, 0.0]]))
     assert e.value.code == inla.E_BADARG
-    bad = synth.config1()[0]
+    bad = synth.poisson_n256_m1000_5pts()[0]
     bad.y = bad.y.copy()
     bad.y[0] = -1.0  # negative count
     with pytest.raises(inla.InlaError) as e:
@@ -152,8 +152,8 @@ def test_bad_arguments_are_rejected():
 
 
 @pytest.mark.slow
-def test_config2_fd_points_subset():
-    spec, thetas = synth.config2()
+def test_n4096_fd_points_subset():
+    spec, thetas = synth.poisson_n4096_m20000_fd7()
     sub = thetas[[0, 3]]
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], sub)
@@ -161,8 +161,8 @@ def test_config2_fd_points_subset():
 
 
 @pytest.mark.slow
-def test_config3_one_point():
-    spec, thetas = synth.config3()
+def test_spacetime_one_point():
+    spec, thetas = synth.spacetime_n8149_m8000_fd13()
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], thetas[:1])
     _check(spec, thetas[:1], lp, st, xs, vs, x_tol=CONSTRAINED_X_TOL, v_rtol=CONSTRAINED_V_RTOL)

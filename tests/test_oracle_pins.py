@@ -346,7 +346,7 @@ def test_constraint_counts_match_null_space_dimensions():
 
 
 def test_workload_constraints_span_the_intrinsic_null_spaces():
-    spec, _ = synth.config3()
+    spec, _ = synth.spacetime_n8149_m8000_fd13()
     C = sp.csr_matrix((spec.C.val, spec.C.col, spec.C.rowptr), shape=(spec.k, spec.n))
     assert spec.k == 1486 and spec.n == 8149
     # C Q_p = eps C for the intrinsic blocks, i.e. C R = 0 blockwise
@@ -373,7 +373,7 @@ def test_workload_constraints_span_the_intrinsic_null_spaces():
 # ---------------------------------------------------------------------------------
 
 def test_log_post_invariant_to_latent_permutation():
-    spec, thetas = synth.config1()
+    spec, thetas = synth.poisson_n256_m1000_5pts()
     r = O.evaluate(spec, thetas[1], want_var=True)
     perm = np.random.default_rng(3).permutation(255)
     blk = spec.blocks[1]
