@@ -254,7 +254,7 @@ def search_with_surrogate(exact: ExactCounter, surrogate: Surrogate, theta0, gto
        proposal is accepted if its exact log pi~ beats theta0's; otherwise the search starts
        from theta0 (its gradient costs one more batch).
     3. Exact BFGS with FD gradients from there, its initial inverse Hessian taken from the
-       surrogate (the exact evaluation remains the judge of every step).
+       surrogate (the exact evaluation still decides every step).
     Returns (theta, exact log pi~, sequential exact calls of the search)."""
     th0 = np.asarray(theta0, dtype=np.float64)
     t = len(th0)
