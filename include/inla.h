@@ -169,7 +169,8 @@ const char *inla_status_string(int status);
  *  Every intermediate lives in one static device array of ~7.4 MB that each GPU loading the
  *  library holds until the process exits; the call allocates nothing (no cudaMalloc, no
  *  library allocator).  The first call on a device looks that array's address up
- *  (cudaGetSymbolAddress), so make it before any stream capture.  All calls share the array
+ *  (cudaGetSymbolAddress), so make it before any stream capture; host threads may make their
+ *  first calls at the same time (the address is stored atomically).  All calls share the array
  *  and it keeps the last call's contents: calls that overlap on the GPU (other streams,
  *  other host threads) race.  The call synchronizes `stream` before returning;
  *  INLA_E_TIMEOUT if a bounded device-side wait gave up. */

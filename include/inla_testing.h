@@ -68,6 +68,13 @@ int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
  * captures, whose timings would mislead the tuner), and this returns it. */
 int inla_test_outer_block(int32_t n_pad, int32_t slices);
 
+/* One cooperative double-float triangular solve of the mixed path on a caller-given lower
+ * factor L (host, row-major n x n FP64, n a multiple of 64): x = L^-1 b (backward = 0) or
+ * x = L^-T b (backward = 1).  Every wait of a tile on an earlier tile's ready flag gives up
+ * after spin_limit polls (0: at once); a wait that gave up makes the call return
+ * INLA_E_TIMEOUT (x untouched) with the device still usable. */
+int inla_test_trsv_df(const double *L, const double *b, int32_t n, int32_t backward, int64_t spin_limit, double *x);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,9 @@ def _needs(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(HERE, "..", "include", "inla.h")]
+    # every header a translation unit can include: csrc/*.h, csrc/*.cuh and the public include/*.h
+    headers = (sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+               sorted(glob.glob(os.path.join(HERE, "..", "include", "*.h"))))
     nvcc = _nvcc()
     jobs = []
     objs = []

@@ -1,6 +1,7 @@
 // Internal declarations of libinla (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <vector>
 #include <string>
@@ -29,6 +30,24 @@ constexpr int MAX_KRON = 8;
   } while (0)
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Kernel attributes (the dynamic shared-memory limit) and launch geometry belong to the device
+// that was current when they were set or queried.  DeviceFlags records a one-time set-up per
+// device (indices 0..63; others are never marked, so their set-up runs on every call).
+inline int current_device() {
+  int d = -1;
+  return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+class DeviceFlags {
+ public:
+  bool test(int dev) const { return dev >= 0 && dev < 64 && ((bits_.load(std::memory_order_acquire) >> dev) & 1u); }
+  void set(int dev) {
+    if (dev >= 0 && dev < 64) bits_.fetch_or(uint64_t(1) << dev, std::memory_order_acq_rel);
+  }
+
+ private:
+  std::atomic<uint64_t> bits_{0};
+};
 
 // Structured prior entry of Q_p (lower triangle, internal indices):
 // value = a + b * exp(theta[t])  (t < 0: value = a)

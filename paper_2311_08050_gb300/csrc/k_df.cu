@@ -545,13 +545,18 @@ void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t
   count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, 0, st>>>(slots, sel, kt);
 }
 int launch_trsv_df(const TrsvArgs& a, cudaStream_t st) {
-  static int per_sm = 0, sms = 0;
-  if (!per_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_df, 256, 0) != cudaSuccess || per_sm <= 0)
+  // resident blocks per SM and SM count, per device (the cooperative grid must fit at once)
+  static std::atomic<int> geo[64][2];
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return INLA_E_CUDA;
+  int per_sm = geo[dev][0].load(), sms = geo[dev][1].load();
+  if (per_sm <= 0 || sms <= 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_df, 256, 0) != cudaSuccess || per_sm <= 0 ||
+        sms <= 0)
       return INLA_E_CUDA;
+    geo[dev][0].store(per_sm);
+    geo[dev][1].store(sms);
   }
   const int items = a.T * a.nslots;
   if (items <= 0) return INLA_OK;

@@ -468,12 +468,12 @@ static int tri(int t) { return t * (t + 1) / 2; }
 
 void launch_potrf_diag(Slot* slots, int nslots, int sel, int kt, int max_t, cudaStream_t st) {
   (void)max_t;
-  static bool init = false;
+  static DeviceFlags attr_set;  // the shared-memory limit is a per-device attribute
   const int smem = 2 * TB * (TB + 1) * (int)sizeof(double);
-  if (!init) {
-    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    init = true;
-  }
+  const int dev = current_device();
+  if (!attr_set.test(dev) &&
+      cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess)
+    attr_set.set(dev);
   count_launch("k_potrf_diag"), k_potrf_diag<<<nslots, 256, smem, st>>>(slots, sel, kt);
 }
 void launch_trsm_panel(Slot* slots, int nslots, int sel, int kt, int max_t, cudaStream_t st) {

@@ -247,13 +247,14 @@ size_t fwd_smem() { return (size_t)(H * H + TS * H + TS * INLA_MLP_MAX_DIN + TS 
 size_t bwd_smem() { return (size_t)(H * H + TS * H + TS * INLA_MLP_MAX_DIN * 4) * sizeof(float); }
 
 int set_smem_attrs() {
-  static bool done = false;
-  if (done) return INLA_OK;
+  static DeviceFlags done;  // the shared-memory limits are per-device attributes
+  const int dev = current_device();
+  if (done.test(dev)) return INLA_OK;
   if (cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem()) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_bwd_delta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem()) !=
           cudaSuccess)
     return INLA_E_CUDA;
-  done = true;
+  done.set(dev);
   return INLA_OK;
 }
 

@@ -689,26 +689,27 @@ int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S, int b
 }
 
 static int num_sms() {
-  static int cached[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-  if (!cached[dev]) {
-    int v = 0;
+  static std::atomic<int> cached[64];
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return 148;
+  int v = cached[dev].load();
+  if (v <= 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-    cached[dev] = v;
+    cached[dev].store(v);
   }
-  return cached[dev];
+  return v;
 }
 
 // Persistent launch: one CTA per SM (shared memory allows no second), tiles round-robin.
 template <int S, int BN>
 static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs& a, int nslots, cudaStream_t st) {
   constexpr int smem = OzCfg<S, BN>::SMEM;
-  static bool init = false;
-  if (!init) {
+  static DeviceFlags attr_set;  // the shared-memory limit is a per-device attribute
+  const int dev = current_device();
+  if (!attr_set.test(dev)) {
     if (cudaFuncSetAttribute(k_ozaki_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return INLA_E_CUDA;
-    init = true;
+    attr_set.set(dev);
   }
   if (a.tiles_total <= 0) return INLA_OK;
   const int grid = std::min(a.tiles_total, num_sms());

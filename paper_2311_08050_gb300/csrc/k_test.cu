@@ -129,3 +129,96 @@ extern "C" int inla_test_cov_df(const double* points, int32_t n, double sigma2, 
   return rc;
 }
 
+
+// One cooperative double-float triangular solve (the Newton-step solve of the mixed path) on a
+// caller-given factor: x = L^-1 b (backward = 0) or L^-T b (backward = 1), every dependency wait
+// bounded by spin_limit iterations.  The 64 x 64 diagonal-tile inverses the kernel needs are
+// formed here on the host by forward substitution (test set-up, not the product path).
+extern "C" int inla_test_trsv_df(const double* L, const double* b, int32_t n, int32_t backward, int64_t spin_limit,
+                                 double* x) {
+  if (!L || !b || !x || n <= 0 || (n % TB) || spin_limit < 0) return INLA_E_BADARG;
+  const int T = n / TB;
+  std::vector<double> linv((size_t)n * TB, 0.0);
+  for (int t = 0; t < T; ++t) {
+    double* Y = &linv[(size_t)t * TB * TB];  // inverse of the diagonal tile t (lower)
+    for (int c = 0; c < TB; ++c) {
+      for (int i = c; i < TB; ++i) {
+        double s = i == c ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) s -= L[(size_t)(t * TB + i) * n + t * TB + k] * Y[k * TB + c];
+        const double d = L[(size_t)(t * TB + i) * n + t * TB + i];
+        if (!(d != 0.0)) return INLA_E_BADARG;
+        Y[i * TB + c] = s / d;
+      }
+    }
+  }
+  double *dL = nullptr, *dLinv = nullptr, *dv = nullptr, *dout = nullptr;
+  Slot* dslot = nullptr;
+  int32_t *flags = nullptr, *err = nullptr, *info = nullptr;
+  int rc = INLA_OK;
+  do {
+    if (cudaMalloc(&dL, (size_t)n * n * 8) || cudaMalloc(&dLinv, (size_t)n * TB * 8) || cudaMalloc(&dv, (size_t)n * 16) ||
+        cudaMalloc(&dout, 64) || cudaMalloc(&dslot, sizeof(Slot)) || cudaMalloc(&flags, sizeof(int32_t) * T) ||
+        cudaMalloc(&err, 4) || cudaMalloc(&info, 8)) {
+      rc = INLA_E_NOMEM;
+      break;
+    }
+    // L and the tile inverses as double-float cells (8 bytes each)
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, (size_t)n * n * 8)) {
+      rc = INLA_E_NOMEM;
+      break;
+    }
+    cudaMemcpy(tmp, L, (size_t)n * n * 8, cudaMemcpyHostToDevice);
+    k_f64_to_df<<<256, 256>>>(tmp, reinterpret_cast<float2*>(dL), (int64_t)n * n);
+    cudaMemcpy(tmp, linv.data(), (size_t)n * TB * 8, cudaMemcpyHostToDevice);
+    k_f64_to_df<<<256, 256>>>(tmp, reinterpret_cast<float2*>(dLinv), (int64_t)n * TB);
+    cudaDeviceSynchronize();
+    cudaFree(tmp);
+    cudaMemcpy(dv, b, (size_t)n * 8, cudaMemcpyHostToDevice);
+    cudaMemset(err, 0, 4);
+    Slot s;
+    std::memset(&s, 0, sizeof(s));
+    s.L = dL;
+    s.Linv = dLinv;
+    s.g = dv;
+    s.t1 = dv + n;
+    s.out = reinterpret_cast<double*>(dout);
+    s.info = info;
+    s.n_pad = s.n = n;
+    s.active = 1;
+    cudaMemcpy(dslot, &s, sizeof(Slot), cudaMemcpyHostToDevice);
+    TrsvArgs a;
+    a.slots = dslot;
+    a.sel = SEL_L;
+    a.src = 0;  // g
+    a.dst = 1;  // t1
+    a.nslots = 1;
+    a.T = T;
+    a.backward = backward ? 1 : 0;
+    a.flags = flags;
+    a.err = err;
+    a.spin_limit = spin_limit;
+    if ((rc = launch_trsv_df(a, 0)) != INLA_OK) break;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      rc = INLA_E_CUDA;
+      break;
+    }
+    int herr = 0;
+    cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+    if (herr) {
+      rc = INLA_E_TIMEOUT;
+      break;
+    }
+    cudaMemcpy(x, dv + n, (size_t)n * 8, cudaMemcpyDeviceToHost);
+  } while (0);
+  cudaFree(dL);
+  cudaFree(dLinv);
+  cudaFree(dv);
+  cudaFree(dout);
+  cudaFree(dslot);
+  cudaFree(flags);
+  cudaFree(err);
+  cudaFree(info);
+  if (rc == INLA_E_CUDA) cudaGetLastError();
+  return rc;
+}

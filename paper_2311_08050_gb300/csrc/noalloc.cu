@@ -7,6 +7,7 @@
 // the output and keeps every intermediate (BF16 slice planes, exponents, the double-float
 // product, an error flag) in one file-scope static __device__ array of fixed size, which
 // every GPU that loads the library holds until the process exits.
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include "../../include/inla.h"
@@ -34,8 +35,10 @@ constexpr size_t kScratchBytes = align256(kOffErr + sizeof(int32_t));  // ~7.4 M
 // kernels receive the address that cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The array's device address, looked up once per device (with that device current).  Atomic: two
+// host threads making their first call at once may both look it up; both store the same value.
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+std::atomic<void*> g_scratch_addr[kMaxDevices];
 
 __global__ void k_noalloc_df_to_f64(const float2* src, double* dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -56,15 +59,15 @@ extern "C" int inla_ozaki_gemm_noalloc(const double* A, const double* B, double*
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return INLA_E_CUDA;
   // set-up, once per device, with that device current
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+  void* addr = g_scratch_addr[dev].load();
+  if (!addr) {
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
       cudaGetLastError();
       return INLA_E_CUDA;
     }
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(addr);
   }
-  char* base = static_cast<char*>(g_scratch_addr[dev]);
+  char* base = static_cast<char*>(addr);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int S = slices;
   const int ldk = K;  // K is a multiple of 64
@@ -79,6 +82,8 @@ extern "C" int inla_ozaki_gemm_noalloc(const double* A, const double* B, double*
   if (cudaMemsetAsync(err, 0, sizeof(int32_t), st) != cudaSuccess) return INLA_E_CUDA;
   oz_slice_f64(A, 0, K, 0, 0, M, K, false, oa, S, 1, st);
   oz_slice_f64(B, 0, K, 0, 0, N, K, false, ob, S, 1, st);
+  // a launch-configuration error does not stick to the stream: check each launch
+  if (cudaPeekAtLastError() != cudaSuccess) return note_launch_error("noalloc slicing");
   OzArgs a;
   std::memset(&a, 0, sizeof(a));
   a.C = cdf;
@@ -95,6 +100,7 @@ extern "C" int inla_ozaki_gemm_noalloc(const double* A, const double* B, double*
   if (rc != INLA_OK) return rc;
   count_launch("k_noalloc_df_to_f64");
   k_noalloc_df_to_f64<<<128, 256, 0, st>>>(cdf, C, (int64_t)M * N);
+  if (cudaPeekAtLastError() != cudaSuccess) return note_launch_error("noalloc conversion");
   int32_t herr = 0;
   if (cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {

@@ -369,6 +369,63 @@ def test_workload_constraints_span_the_intrinsic_null_spaces():
 
 
 # ---------------------------------------------------------------------------------
+# structure matrices by value (Section 5.1 structures; Appendix C prints RW1(4))
+# ---------------------------------------------------------------------------------
+
+def test_rw1_structure_equals_appendix_c_printed_precision():
+    """Appendix C's prior precision Q_e of four effects is the RW1 structure of size 4."""
+    g = _read_golden("appendix_c_example.txt")
+    R = O.structure_matrix(Factor("rw1", 4))
+    assert np.array_equal(R, g["Qe"])
+
+
+def test_rw2_structure_is_the_second_difference_stencil():
+    """RW2 of size 5, written out by hand: the boundary rows (1, -2, 1) and (-2, 5, -4, 1),
+    the interior row (1, -4, 6, -4, 1), and their mirror images."""
+    R_hand = np.array([[1, -2, 1, 0, 0],
+                       [-2, 5, -4, 1, 0],
+                       [1, -4, 6, -4, 1],
+                       [0, 1, -4, 5, -2],
+                       [0, 0, 1, -2, 1]], dtype=float)
+    assert np.array_equal(O.structure_matrix(Factor("rw2", 5)), R_hand)
+
+
+def test_icar_structure_is_degree_minus_adjacency_by_hand():
+    """Besag/ICAR on a hand-drawn 5-node graph with edges 0-1, 0-2, 1-2, 2-3, 3-4: the
+    diagonal holds the neighbour counts (2, 2, 3, 2, 1), each edge a -1."""
+    edges = [(0, 1), (0, 2), (1, 2), (2, 3), (3, 4)]
+    nbrs = [sorted([b for a, b in edges if a == i] + [a for a, b in edges if b == i]) for i in range(5)]
+    graph = CSR.from_rows(5, 5, [np.array(v) for v in nbrs], [np.ones(len(v)) for v in nbrs])
+    R_hand = np.array([[2, -1, -1, 0, 0],
+                       [-1, 2, -1, 0, 0],
+                       [-1, -1, 3, -1, 0],
+                       [0, 0, -1, 2, -1],
+                       [0, 0, 0, -1, 1]], dtype=float)
+    assert np.array_equal(O.structure_matrix(Factor("icar", 5, graph)), R_hand)
+    assert np.array_equal(O.structure_matrix(Factor("iid", 3)), np.eye(3))
+
+
+def test_kronecker_block_entries_follow_the_latent_order():
+    """A kron block of factors (F1, F2) orders the latent effects with the last factor
+    fastest: entry ((i1, i2), (j1, j2)) at (i1 n2 + i2, j1 n2 + j2) is
+    tau R1[i1, j1] R2[i2, j2] (+ eps on the diagonal); checked entry by entry on RW1(3) x
+    RW2(4) against the hand-written stencils, tau = 2, eps = 0.5."""
+    rw1 = {(0, 0): 1, (1, 1): 2, (2, 2): 1, (0, 1): -1, (1, 0): -1, (1, 2): -1, (2, 1): -1}
+    rw2 = np.array([[1, -2, 1, 0], [-2, 5, -4, 1], [1, -4, 5, -2], [0, 1, -2, 1]], dtype=float)
+    blk = Block("kron", 12, theta_idx=0, factors=[Factor("rw1", 3), Factor("rw2", 4)], eps=0.5)
+    spec = ModelSpec("kron_pin", 12, "gaussian", CSR(0, 12, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                                                      np.zeros(0)), np.zeros(0), None, [blk], [("gauss", 0, 1)])
+    Qp, logdet = O.prior_precision(spec, np.array([math.log(2.0)]))
+    for i1 in range(3):
+        for i2 in range(4):
+            for j1 in range(3):
+                for j2 in range(4):
+                    want = 2.0 * rw1.get((i1, j1), 0) * rw2[i2, j2] + (0.5 if (i1, i2) == (j1, j2) else 0.0)
+                    assert Qp[i1 * 4 + i2, j1 * 4 + j2] == pytest.approx(want, abs=1e-14)
+    assert logdet == pytest.approx(np.linalg.slogdet(Qp)[1], rel=1e-12)
+
+
+# ---------------------------------------------------------------------------------
 # invariance
 # ---------------------------------------------------------------------------------
 

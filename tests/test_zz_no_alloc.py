@@ -30,7 +30,10 @@ def test_noalloc_gemm_matches_allocating_entry_point_twice():
     L.inla_test_ozaki_gemm.argtypes = [P, P, P] + [C.c_int32] * 8 + [C.c_double, C.c_double]
     L.inla_ozaki_gemm_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p] + [C.c_int32] * 4 + [C.c_void_p]
     rng = np.random.default_rng(2024)
-    shapes = [(300, 200, 320, 5), (512, 448, 512, 4)]
+    # the largest call first, then a smaller ragged one: whatever the first call leaves in the
+    # shared static array (planes, exponents and product of a 512 x 512 x 512 problem) must not
+    # reach the second call's result
+    shapes = [(512, 512, 512, 5), (300, 200, 320, 4)]
     for M, N, K, S in shapes:
         A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-2, 2, (M, 1)))
         Bm = rng.standard_normal((N, K)) * np.exp(rng.uniform(-2, 2, (N, 1)))
