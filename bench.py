@@ -103,10 +103,13 @@ def _dist_env():
 
 BENCH_WORKLOAD = "poisson_n16384_m100000_fd9"
 CAPTURE_WORKLOADS = ("poisson_n4096_m20000_fd7", "poisson_n256_m1000_5pts")
-# ncu capture of the current GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum, mean over
-# all 5613 GEMM launches of one n = 16384 step, outer block 512 as tuned); retake after any change
-# to the kernel or the blocking
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = {BENCH_WORKLOAD: 0.8323e9}
+# DRAM traffic of the GEMM as a multiple of its compulsory bytes (slice planes read once, C
+# written and read once), from one small ncu capture of the dominant shape (the trailing update
+# C -= P P^T, 8192 x 8192 lower, K = 512, S = 4, three launches).  The step's traffic per launch
+# is this ratio times the step's compulsory bytes per launch (counted by the library for every
+# launch).  Set to None when the kernel changes, until the capture is taken again.
+GEMM_TRAFFIC_RATIO = 0.985
+GEMM_TRAFFIC_PROFILE = "profiles/k_ozaki_gemm_syrk_8192x512_s4_traffic.md"
 
 
 def _workload(rank, workload=BENCH_WORKLOAD):
@@ -220,7 +223,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     L.inla_test_stats_enable(0)
     L.inla_test_profile_enable(0)
-    stats = (C.c_double * 4)()
+    stats = (C.c_double * 5)()
     L.inla_test_stats_read(stats)
     pbuf = C.create_string_buffer(1 << 16)
     L.inla_test_profile_read(pbuf, 1 << 16)
@@ -231,23 +234,41 @@ def run_ours(args):
     step_ms_prof = sum(b["ms"] for b in breakdown) or 1.0
     for b in breakdown:
         b["share"] = round(b["ms"] / step_ms_prof, 4)
-    launches, alg, tens, kms = stats[0], stats[1], stats[2], stats[3]
+    launches, alg, tens, kms, alg_bytes = stats[0], stats[1], stats[2], stats[3], stats[4]
     peaks, psrc = _peaks()
     peak_tc = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     tens_rate = tens / (kms / 1e3) / 1e12 if kms > 0 else None
     alg_rate = alg / (kms / 1e3) / 1e12 if kms > 0 else None
-    # DRAM bytes per GEMM launch, measured by ncu over every GEMM launch of one step of the
-    # n = 16384 workload (profiles/k_ozaki_gemm_launch_traffic_n16384.md); other workloads: none
-    traffic = GEMM_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload)
+    # DRAM bytes per GEMM launch: the compulsory bytes of this step's launches (counted per launch
+    # by the library) times the traffic ratio of the small ncu capture of the dominant shape
+    alg_bytes_per_launch = alg_bytes / launches if launches else None
+    traffic = GEMM_TRAFFIC_RATIO * alg_bytes_per_launch if (GEMM_TRAFFIC_RATIO and alg_bytes_per_launch) else None
     n_pad = ((spec.n + 255) // 256) * 256
     outer_block = {f"slices{sl}": int(L.inla_test_outer_block(n_pad, sl)) for sl in (args.newton_slices, args.slices)}
+    # achieved = the method's flops (2 x needed output elements x K per GEMM launch, i.e. the
+    # Cholesky / inverse / product work itself) per second of GEMM time; the BF16 slice passes
+    # the tensor pipe runs for them are reported separately
     roofline = {"bound": "tensor", "kernel": "k_ozaki_gemm<S> (tcgen05 BF16 slices)",
-                "achieved": tens_rate, "peak": peak_tc, "unit": "TFLOP/s",
-                "frac": (tens_rate / peak_tc) if tens_rate else None, "traffic": traffic,
-                "traffic_unit": "bytes per launch (dram read + write, ncu)" if traffic else None,
-                "algorithmic_tflops": alg_rate, "passes_per_flop": round(tens / alg, 2) if alg else None,
+                "achieved": alg_rate, "peak": peak_tc, "unit": "TFLOP/s",
+                "frac": (alg_rate / peak_tc) if alg_rate else None,
+                "frac_algorithmic": (alg_rate / peak_tc) if alg_rate else None,
+                "traffic": traffic,
+                "traffic_unit": "bytes per launch (dram read + write)" if traffic else None,
+                "traffic_source": (f"{GEMM_TRAFFIC_RATIO:.3f} x compulsory bytes per launch "
+                                   f"({alg_bytes_per_launch:.4g}); ratio from {GEMM_TRAFFIC_PROFILE}")
+                if traffic else "no capture of the current kernel",
+                "tensor_pipe_tflops": tens_rate, "frac_tensor_pipe": (tens_rate / peak_tc) if tens_rate else None,
+                "passes_per_flop": round(tens / alg, 2) if alg else None,
                 "launches_per_step": int(launches), "kernel_ms_per_step": kms,
-                "peak_source": f"{psrc} bf16 sustained (kernel timed inside a long step)"}
+                "compulsory_bytes_per_step": alg_bytes,
+                "peak_source": f"{psrc} bf16 sustained (kernel timed inside a long step), of measured"
+                if psrc == "measured" else "fallback bf16 sustained"}
+    # FP64 pipe peak, measured here by the library's FMA probe (no device setting changed)
+    fp64_peak = C.c_double(0.0)
+    fp32_peak = C.c_double(0.0)
+    L.inla_test_fma_peak.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double)]
+    L.inla_test_fma_peak(0, 3, C.byref(fp64_peak))
+    L.inla_test_fma_peak(1, 3, C.byref(fp32_peak))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -285,9 +306,23 @@ def run_ours(args):
                                            x_out=[x64[0].data_ptr()], var_out=[v64[0].data_ptr()])
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
+        # the FP64 path refactors at every Newton iteration: its algorithmic flops are the prior
+        # inversion (Cholesky, triangular inverse, W^T W: n_c^3), one n^3/3 Cholesky per
+        # iteration plus the final one, and the triangular inverse for the variances (n^3/3)
+        L.inla_test_newton_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+        iters64 = int(L.inla_test_newton_trace(None, None, 0))
+        n_c = sum(b.size for b in spec.blocks if b.kind == "dense_exp")
+        f64_flops = float(n_c) ** 3 + (iters64 + 1) * n ** 3 / 3.0 + n ** 3 / 3.0
+        f64_rate = f64_flops / t64 / 1e12
         out["fp64"] = {"value": 1.0 / t64, "unit": UNIT, "thetas_timed": 1, "seconds": t64,
                        "log_post_theta0": float(lp64[0]), "status": int(st64[0]),
-                       "mixed_minus_fp64_log_post": float(lp[0] - lp64[0])}
+                       "mixed_minus_fp64_log_post": float(lp[0] - lp64[0]), "newton_iterations": iters64,
+                       "algorithmic_tflop": f64_flops / 1e12}
+        roofline["fp64"] = {"bound": "fp64 alu", "achieved": f64_rate, "peak": fp64_peak.value, "unit": "TFLOP/s",
+                            "frac": f64_rate / fp64_peak.value if fp64_peak.value > 0 else None,
+                            "what": "FP64 GPU path, whole theta evaluation: algorithmic flops / wall time",
+                            "peak_source": "measured in this run by the library's DFMA probe (inla_test_fma_peak)"}
+    roofline["fp32_fma_peak_tflops"] = fp32_peak.value
     # ---------------- FP64 CPU oracle on the host cores (rank 0) ----------------
     if rank == 0 and not args.no_cpu:
         from oracle import inla_oracle as O
@@ -338,12 +373,15 @@ def run_gemm(args):
                                         0, 0, lower, 0, 1.0 if accumulate else 0.0, -1.0 if accumulate else 1.0)
             assert rc == 0
         L.inla_test_stats_enable(0)
-        st = (C.c_double * 4)()
+        st = (C.c_double * 5)()
         L.inla_test_stats_read(st)
         ms = st[3]
         tens = st[2] / (ms / 1e3) / 1e12
-        res.append({"M": M, "N": N, "K": K, "S": S, "lower": lower, "accumulate": accumulate, "ms": ms, "tensor_tflops": tens,
-                    "alg_tflops": st[1] / (ms / 1e3) / 1e12, "frac_bf16_burst": tens / peaks["bf16_tflops"]})
+        alg_t = st[1] / (ms / 1e3) / 1e12
+        res.append({"M": M, "N": N, "K": K, "S": S, "lower": lower, "accumulate": accumulate, "ms": ms,
+                    "alg_tflops": alg_t, "frac_algorithmic_bf16_burst": alg_t / peaks["bf16_tflops"],
+                    "tensor_tflops": tens, "frac_tensor_pipe_bf16_burst": tens / peaks["bf16_tflops"],
+                    "compulsory_bytes": st[4], "compulsory_gbs": st[4] / (ms / 1e3) / 1e9})
     print(json.dumps({"gemm_microbench": res}), flush=True)
 
 

@@ -69,6 +69,8 @@ extern "C" {
                            updates, double-float storage, FP64 small diagonal blocks */
 
 #define INLA_OPT_DEVICE_OUT 1  /* x_hat / mean / var outputs are device pointers */
+#define INLA_OPT_NO_SHARED_START 2  /* INLA_MIXED: every point runs Newton from x = 0 with its
+                                       own factorisations (see inla_eval_batch) */
 
 typedef struct {
   int32_t kind;                 /* INLA_FACTOR_* */
@@ -144,7 +146,13 @@ int inla_eval_theta(inla_model *model, const double *theta, const inla_opts *opt
  * nmodels == 1).  All points run together on the device.  log_post[b] and status[b]
  * (INLA_OK or a negative code for that point alone) are always written; x_hat[b] and
  * var[b] (n of that model doubles each) are written when the arrays and entries are
- * non-NULL.  The call returns INLA_OK if the batch ran, even when single points failed. */
+ * non-NULL.  The call returns INLA_OK if the batch ran, even when single points failed.
+ * INLA_MIXED, Poisson models with several points in the call: the first point of the model
+ * runs Newton from x = 0; the others then start from its mode and iterate with its final
+ * factor (modified Newton: the gradient is each point's own and exact, so each converges to
+ * its own mode to the same step tolerance), taking factorisations of their own only if the
+ * steps stop shrinking 4x per iteration.  For the 2t + 1 points of a finite-difference stencil
+ * this replaces most Newton-step factorisations.  INLA_OPT_NO_SHARED_START turns it off. */
 int inla_eval_batch(inla_model *const *models, int32_t nmodels, const int32_t *model_of_theta,
                     const double *thetas, int32_t B, const inla_opts *opts,
                     double *log_post, int32_t *status, double *const *x_hat,

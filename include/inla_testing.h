@@ -31,9 +31,11 @@ const char *inla_test_debug_site(void);
 
 /* Launch statistics of the Ozaki-split tensor-core GEMM (the dominant kernel of the mixed
  * path).  While enabled, CUDA events are recorded around every launch on its stream.
- * inla_test_stats_read fills out[0..3] = {launches, algorithmic flops (2 * needed output
+ * inla_test_stats_read fills out[0..4] = {launches, algorithmic flops (2 * needed output
  * elements * K), tensor-pipe flops (algorithmic * S(S+1)/2 BF16 passes), summed launch
- * time in ms}, synchronizing on the recorded events, and resets the counters. */
+ * time in ms, compulsory DRAM bytes (slice planes of both operands read once, the needed
+ * double-float C elements written once and, when accumulating, read once)}, synchronizing on
+ * the recorded events, and resets the counters. */
 void inla_test_stats_enable(int on);
 int inla_test_stats_read(double *out);
 
@@ -62,8 +64,9 @@ int inla_test_cov_df(const double *points, int32_t n, double sigma2, double inv_
 int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
 
 /* The outer block (panel width) the mixed Cholesky chose for matrices of padded size n_pad
- * factored with `slices` slices: 256 or 512 once its two timed candidate runs are complete,
- * 0 while undecided (sizes below 1024 always use 256).  With the environment variable
+ * factored with `slices` slices (tuned per batch size; this returns the choice for the largest
+ * batch decided): 256 or 512 once its two timed candidate runs are complete, 0 while undecided
+ * (sizes below 1024 always use 256).  With the environment variable
  * INLA_OUTER_BLOCK=256 or 512 (read once) every size uses that block, untuned (for profiler
  * captures, whose timings would mislead the tuner), and this returns it. */
 int inla_test_outer_block(int32_t n_pad, int32_t slices);
@@ -74,6 +77,11 @@ int inla_test_outer_block(int32_t n_pad, int32_t slices);
  * after spin_limit polls (0: at once); a wait that gave up makes the call return
  * INLA_E_TIMEOUT (x untouched) with the device still usable. */
 int inla_test_trsv_df(const double *L, const double *b, int32_t n, int32_t backward, int64_t spin_limit, double *x);
+
+/* Arithmetic peak probe: best of `reps` timed launches (after one warm-up) of a kernel running
+ * eight independent FMA chains per thread on every SM, FP64 (kind 0) or FP32 (kind 1); writes
+ * the rate in TFLOP/s (2 flops per FMA).  Changes no device setting. */
+int inla_test_fma_peak(int32_t kind, int32_t reps, double *tflops);
 
 #ifdef __cplusplus
 }

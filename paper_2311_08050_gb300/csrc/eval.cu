@@ -245,7 +245,7 @@ static int read_outputs(Batch& B, std::vector<double>& out, std::vector<int32_t>
   return e ? INLA_E_TIMEOUT : INLA_OK;
 }
 
-static void fail_slot(Batch& B, std::vector<int>& status, int i, int code) {
+static void fail_slot(Batch& B, int* status, int i, int code) {
   if (status[i] == INLA_OK) status[i] = code;
   B.h[i].active = 0;
 }
@@ -257,8 +257,171 @@ static double objective(const ModelDev& md, const double* out) {
   return f;
 }
 
+// Slots [lo, hi) of a batch as a batch of their own: the strided routines see them as slots
+// 0 .. hi - lo - 1 (slot lo's matrices are the view's base; the slice workspaces are shared and
+// their slot numbering restarts).  Host-side changes to the view's slots are copied back by
+// copy_back.
+static Batch view_of(const Batch& B, int lo, int hi) {
+  Batch V = B;
+  V.d_slots = B.d_slots + lo;
+  V.h.assign(B.h.begin() + lo, B.h.begin() + hi);
+  V.n = hi - lo;
+  return V;
+}
+static void copy_back(Batch& B, const Batch& V, int lo) {
+  for (int i = 0; i < V.n; ++i) B.h[lo + i] = V.h[i];
+}
+// the factor of Q* and the constraint Schur matrices a slot's solves read
+static void set_factor_ptrs(Slot& dst, const Slot& src) {
+  dst.L = src.L;
+  dst.Linv = src.Linv;
+  dst.Z = src.Z;
+  dst.S = src.S;
+  dst.SLinv = src.SLinv;
+}
+
+// Newton iterations of Algorithm 1 over the slots of V (all active on entry), each step
+// x_new = x + Q*(x)^-1 grad f(x), kriged when constrained, halved while the objective falls.
+// start_shared: the slots start from the x the caller set, with the factor (and Schur matrices)
+// their pointers name -- another point's final factor, read only -- and keep it while the steps
+// shrink at least 4x per iteration (modified Newton: the gradient is exact, so the fixed point
+// is still the mode); `own` then holds their own matrix pointers, restored before the first
+// factorisation of their own.
+static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts& o, int* status, int* iters,
+                        int* converged, int* d_flags, bool start_shared, const std::vector<Slot>& own) {
+  const int NB = V.n;
+  std::vector<double> out;
+  std::vector<int32_t> info;
+  V.S = V.S_newton;
+  if (!start_shared) launch_zero_vec(V.d_slots, NB, 0, V.max_n, V.st);
+  launch_eval_lik(V.d_slots, NB, 0, V.max_m, V.st);
+  op_qp_gemv(V, 0);
+  INLA_TRY(read_outputs(V, out, info));
+  std::vector<double> f_old(NB);
+  for (int i = 0; i < NB; ++i) f_old[i] = objective(*models[i], &out[(size_t)i * SLOT_NOUT]);
+  std::vector<int> flags(NB, 0);
+  int rc = INLA_OK;
+  double last_step = 1e300;
+  bool reuse_ok = true;
+  bool shared = start_shared;
+  int it_own = start_shared ? -1 : 1;  // iteration of the first factorisation of the slots' own
+  for (int it = 1; it <= o.newton_max && rc == INLA_OK; ++it) {
+    int nact = 0;
+    for (int i = 0; i < NB; ++i) nact += V.h[i].active;
+    if (nact == 0) break;
+    for (int i = 0; i < NB; ++i)
+      if (V.h[i].active) iters[i] = it;
+    // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction.  The mixed path reuses the
+    // last factor once the steps are small and shrinking fast (modified Newton): the gradient
+    // stays exact, so the fixed point is unchanged; a reused step that does not shrink the step
+    // by 4x forces a fresh factor at the next iteration.
+    bool refactor;
+    if (shared) {
+      refactor = !reuse_ok;
+      if (refactor) {  // convergence slowed: the slots factor their own Q* from here on
+        for (int i = 0; i < NB; ++i) set_factor_ptrs(V.h[i], own[i]);
+        sync_active(V);
+        shared = false;
+        it_own = it;
+      }
+    } else {
+      refactor = !V.mixed || it - it_own < 2 || last_step > 1e-2 || !reuse_ok;
+    }
+    if (refactor) op_assemble_q(V);
+    launch_gradient(V.d_slots, NB, V.max_n, V.st);
+    if ((rc = debug_check(V.st, "newton assemble")) != INLA_OK) break;
+    if (refactor && (rc = op_potrf(V, SEL_L)) != INLA_OK) break;
+    if ((rc = debug_check(V.st, "newton potrf")) != INLA_OK) break;
+    if ((rc = solve_llt(V, SEL_L, V_G, V_T2, V_G)) != INLA_OK) break;
+    if ((rc = debug_check(V.st, "newton solve")) != INLA_OK) break;
+    launch_newton_xu(V.d_slots, NB, V.max_n, V.st);
+    if (V.max_k > 0) {
+      if (refactor && (rc = op_schur(V)) != INLA_OK) break;
+      launch_cx(V.d_slots, NB, V.max_k, V.st);
+      if ((rc = solve_llt(V, SEL_S, V_KV1, V_KV2, V_KV1)) != INLA_OK) break;
+      if (V.mixed) launch_z_gemv_df(V.d_slots, NB, V.max_n, V.st);
+      else launch_z_gemv(V.d_slots, NB, V.max_n, V.st);
+      if ((rc = solve_lt(V, SEL_L, V_T2, V_G)) != INLA_OK) break;
+      launch_krige_apply(V.d_slots, NB, V.max_n, V.st);
+      if ((rc = debug_check(V.st, "newton kriging")) != INLA_OK) break;
+    }
+    launch_eval_lik(V.d_slots, NB, 1, V.max_m, V.st);
+    op_qp_gemv(V, 1);
+    launch_step_norm(V.d_slots, NB, V.max_n, V.st);
+    if ((rc = read_outputs(V, out, info)) != INLA_OK) break;
+    for (int i = 0; i < NB; ++i)
+      if (V.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(V, status, i, INLA_E_NOT_SPD);
+    // step halving while the objective decreases
+    for (int h = 0; h < 30; ++h) {
+      int any = 0;
+      for (int i = 0; i < NB; ++i) {
+        flags[i] = 0;
+        if (!V.h[i].active || models[i]->likelihood == INLA_LIK_GAUSSIAN) continue;
+        const double fn = objective(*models[i], &out[(size_t)i * SLOT_NOUT]);
+        if (fn < f_old[i] - 1e-10 * (1.0 + std::fabs(f_old[i]))) flags[i] = any = 1;
+      }
+      if (!any) break;
+      cudaMemcpyAsync(d_flags, flags.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, V.st);
+      launch_halve(V.d_slots, NB, d_flags, V.max_n, V.st);
+      launch_eval_lik(V.d_slots, NB, 1, V.max_m, V.st);
+      op_qp_gemv(V, 1);
+      launch_step_norm(V.d_slots, NB, V.max_n, V.st);
+      if ((rc = read_outputs(V, out, info)) != INLA_OK) break;
+    }
+    if (rc != INLA_OK) break;
+    launch_accept(V.d_slots, NB, V.max_n, V.st);
+    {
+      double mx = 0.0;
+      for (int i = 0; i < NB; ++i)
+        if (V.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
+      reuse_ok = (refactor && !shared) || mx < 0.25 * last_step;
+      last_step = mx;
+      g_newton_trace.push_back({mx, refactor ? 1 : 0});
+    }
+    for (int i = 0; i < NB; ++i) {
+      if (!V.h[i].active) continue;
+      const double* oi = &out[(size_t)i * SLOT_NOUT];
+      f_old[i] = objective(*models[i], oi);
+      if (!std::isfinite(f_old[i])) {
+        fail_slot(V, status, i, INLA_E_NO_CONVERGENCE);
+        continue;
+      }
+      if (models[i]->likelihood == INLA_LIK_GAUSSIAN || oi[OUT_STEP] <= o.newton_tol) {
+        converged[i] = 1;
+        V.h[i].active = 0;
+      }
+    }
+    sync_active(V);
+  }
+  if (shared) {  // the slots name their own matrices again
+    for (int i = 0; i < NB; ++i) set_factor_ptrs(V.h[i], own[i]);
+    sync_active(V);
+  }
+  return rc;
+}
+
+// Q* at the mode and its factor (and, with constraints, Z = L^-1 C^T and the factor of
+// S = Z^T Z) for the slots of V that are still healthy; the likelihood and x^T Q_p x at x.
+static int final_factor(Batch& V) {
+  V.S = V.S_exact;
+  sync_active(V);
+  launch_eval_lik(V.d_slots, V.n, 0, V.max_m, V.st);
+  op_qp_gemv(V, 0);
+  op_assemble_q(V);
+  INLA_TRY(op_potrf(V, SEL_L));
+  INLA_TRY(debug_check(V.st, "final potrf"));
+  if (V.max_k > 0) INLA_TRY(op_schur(V));
+  return debug_check(V.st, "final schur");
+}
+
+// One batch: prior precision of every point; Newton to the mode; the factor at the mode;
+// log-determinants, variances and log pi~.  Slots [0, nlead) run Newton from x = 0.  Slots
+// [nlead, NB) ("followers", mixed path only) each name an earlier slot anchor_of[i] of the same
+// model: they start from that slot's mode with its final factor (see newton_phase), which for the
+// points of one finite-difference stencil -- theta apart by the FD step -- converges in a few
+// cheap iterations instead of a Newton factorisation per step.
 static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const inla_opts& o, bool want_var,
-                     std::vector<int>& status, std::vector<int>& iters) {
+                     std::vector<int>& status, std::vector<int>& iters, int nlead, const std::vector<int>& anchor_of) {
   const int NB = B.n;
   std::vector<double> out;
   std::vector<int32_t> info;
@@ -285,127 +448,74 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   launch_prior_logdet(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
   for (int i = 0; i < NB; ++i)
-    if (info[2 * i] & INFO_NOT_SPD) fail_slot(B, status, i, INLA_E_NOT_SPD);
+    if (info[2 * i] & INFO_NOT_SPD) fail_slot(B, status.data(), i, INLA_E_NOT_SPD);
   sync_active(B);
-  // ---------------- Newton iterations ----------------
-  B.S = B.S_newton;
-  launch_zero_vec(B.d_slots, NB, 0, B.max_n, B.st);
-  launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
-  op_qp_gemv(B, 0);
-  INLA_TRY(read_outputs(B, out, info));
-  std::vector<double> f_old(NB);
-  for (int i = 0; i < NB; ++i) f_old[i] = objective(*models[i], &out[(size_t)i * SLOT_NOUT]);
-  std::vector<int> converged(NB, 0);
   int* d_flags = nullptr;
   INLA_CUDA_TRY(cudaMallocAsync((void**)&d_flags, sizeof(int) * NB, B.st));
-  std::vector<int> flags(NB, 0);
-  int rc = INLA_OK;
-  double last_step = 1e300;
-  bool reuse_ok = true;
+  std::vector<int> converged(NB, 0);
   g_newton_trace.clear();
-  for (int it = 1; it <= o.newton_max && rc == INLA_OK; ++it) {
-    int nact = 0;
-    for (int i = 0; i < NB; ++i) nact += B.h[i].active;
-    if (nact == 0) break;
-    for (int i = 0; i < NB; ++i)
-      if (B.h[i].active) iters[i] = it;
-    // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction.  The mixed path reuses
-    // the last factor once the steps are small and shrinking fast (modified Newton): the
-    // gradient stays exact, so the fixed point is unchanged; a reused step that does not
-    // shrink the step by 4x forces a fresh factor at the next iteration.
-    const bool refactor = !B.mixed || it <= 2 || last_step > 1e-2 || !reuse_ok;
-    if (refactor) op_assemble_q(B);
-    launch_gradient(B.d_slots, NB, B.max_n, B.st);
-    if ((rc = debug_check(B.st, "newton assemble")) != INLA_OK) break;
-    if (refactor && (rc = op_potrf(B, SEL_L)) != INLA_OK) break;
-    if ((rc = debug_check(B.st, "newton potrf")) != INLA_OK) break;
-    if ((rc = solve_llt(B, SEL_L, V_G, V_T2, V_G)) != INLA_OK) break;
-    if ((rc = debug_check(B.st, "newton solve")) != INLA_OK) break;
-    launch_newton_xu(B.d_slots, NB, B.max_n, B.st);
-    if (B.max_k > 0) {
-      if (refactor && (rc = op_schur(B)) != INLA_OK) break;
-      launch_cx(B.d_slots, NB, B.max_k, B.st);
-      if ((rc = solve_llt(B, SEL_S, V_KV1, V_KV2, V_KV1)) != INLA_OK) break;
-      if (B.mixed) launch_z_gemv_df(B.d_slots, NB, B.max_n, B.st);
-      else launch_z_gemv(B.d_slots, NB, B.max_n, B.st);
-      if ((rc = solve_lt(B, SEL_L, V_T2, V_G)) != INLA_OK) break;
-      launch_krige_apply(B.d_slots, NB, B.max_n, B.st);
-      if ((rc = debug_check(B.st, "newton kriging")) != INLA_OK) break;
+  int rc = INLA_OK;
+  // ---------------- Newton, leaders ----------------
+  {
+    Batch V = view_of(B, 0, nlead);
+    std::vector<Slot> own(V.h);
+    rc = newton_phase(V, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, false, own);
+    copy_back(B, V, 0);
+  }
+  // a point that failed or did not converge leaves the rest of the evaluation
+  auto settle = [&](int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      if (status[i] == INLA_OK && !converged[i]) status[i] = INLA_E_NO_CONVERGENCE;
+      B.h[i].active = status[i] == INLA_OK;
     }
-    launch_eval_lik(B.d_slots, NB, 1, B.max_m, B.st);
-    op_qp_gemv(B, 1);
-    launch_step_norm(B.d_slots, NB, B.max_n, B.st);
-    if ((rc = read_outputs(B, out, info)) != INLA_OK) break;
-    for (int i = 0; i < NB; ++i)
-      if (B.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(B, status, i, INLA_E_NOT_SPD);
-    // step halving while the objective decreases
-    for (int h = 0; h < 30; ++h) {
-      int any = 0;
-      for (int i = 0; i < NB; ++i) {
-        flags[i] = 0;
-        if (!B.h[i].active || models[i]->likelihood == INLA_LIK_GAUSSIAN) continue;
-        const double fn = objective(*models[i], &out[(size_t)i * SLOT_NOUT]);
-        if (fn < f_old[i] - 1e-10 * (1.0 + std::fabs(f_old[i]))) flags[i] = any = 1;
+  };
+  if (rc == INLA_OK) settle(0, nlead);
+  // ---------------- factor at the leaders' modes; followers from their anchors ----------------
+  if (rc == INLA_OK && nlead < NB) {
+    Batch V = view_of(B, 0, nlead);
+    rc = final_factor(V);
+    copy_back(B, V, 0);
+    if (rc == INLA_OK) {
+      bool anchors_ok = true;
+      for (int i = nlead; i < NB; ++i) anchors_ok = anchors_ok && B.h[anchor_of[i]].active;
+      Batch F = view_of(B, nlead, NB);
+      std::vector<Slot> own(F.h);
+      for (int i = nlead; i < NB; ++i) {
+        if (!B.h[i].active) continue;
+        Slot& f = F.h[i - nlead];
+        if (anchors_ok) {
+          const Slot& a = B.h[anchor_of[i]];
+          cudaMemcpyAsync(f.x, a.x, sizeof(double) * f.n_pad, cudaMemcpyDeviceToDevice, B.st);
+          set_factor_ptrs(f, a);
+        }
       }
-      if (!any) break;
-      cudaMemcpyAsync(d_flags, flags.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, B.st);
-      launch_halve(B.d_slots, NB, d_flags, B.max_n, B.st);
-      launch_eval_lik(B.d_slots, NB, 1, B.max_m, B.st);
-      op_qp_gemv(B, 1);
-      launch_step_norm(B.d_slots, NB, B.max_n, B.st);
-      if ((rc = read_outputs(B, out, info)) != INLA_OK) break;
-    }
-    if (rc != INLA_OK) break;
-    launch_accept(B.d_slots, NB, B.max_n, B.st);
-    {
-      double mx = 0.0;
-      for (int i = 0; i < NB; ++i)
-        if (B.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
-      reuse_ok = refactor || mx < 0.25 * last_step;
-      last_step = mx;
-      g_newton_trace.push_back({mx, refactor ? 1 : 0});
-    }
-    for (int i = 0; i < NB; ++i) {
-      if (!B.h[i].active) continue;
-      const double* oi = &out[(size_t)i * SLOT_NOUT];
-      f_old[i] = objective(*models[i], oi);
-      if (!std::isfinite(f_old[i])) {
-        fail_slot(B, status, i, INLA_E_NO_CONVERGENCE);
-        continue;
-      }
-      if (models[i]->likelihood == INLA_LIK_GAUSSIAN || oi[OUT_STEP] <= o.newton_tol) {
-        converged[i] = 1;
-        B.h[i].active = 0;
+      sync_active(F);
+      rc = newton_phase(F, models.data() + nlead, o, status.data() + nlead, iters.data() + nlead,
+                        converged.data() + nlead, d_flags, anchors_ok, own);
+      copy_back(B, F, nlead);
+      if (rc == INLA_OK) {
+        settle(nlead, NB);
+        Batch G = view_of(B, nlead, NB);
+        rc = final_factor(G);
+        copy_back(B, G, nlead);
       }
     }
-    sync_active(B);
+  } else if (rc == INLA_OK) {
+    rc = final_factor(B);
   }
   cudaFreeAsync(d_flags, B.st);
   if (rc != INLA_OK) return rc;
-  for (int i = 0; i < NB; ++i) {
-    if (status[i] == INLA_OK && !converged[i]) status[i] = INLA_E_NO_CONVERGENCE;
-    B.h[i].active = status[i] == INLA_OK;
-  }
   sync_active(B);
-  // ---------------- at the mode ----------------
+  // ---------------- at the modes: log-determinants, variances, log pi~ ----------------
   B.S = B.S_exact;
-  launch_eval_lik(B.d_slots, NB, 0, B.max_m, B.st);
-  op_qp_gemv(B, 0);
-  op_assemble_q(B);
-  INLA_TRY(op_potrf(B, SEL_L));
   op_logdet(B, SEL_L, OUT_LOGDET_Q);
-  INLA_TRY(debug_check(B.st, "final potrf"));
-  if (B.max_k > 0) {
-    INLA_TRY(op_schur(B));
-    op_logdet(B, SEL_S, OUT_LOGDET_S);
-  }
-  INLA_TRY(debug_check(B.st, "final schur"));
+  if (B.max_k > 0) op_logdet(B, SEL_S, OUT_LOGDET_S);
   if (want_var) INLA_TRY(op_variances(B));
   INLA_TRY(debug_check(B.st, "final variances"));
   launch_assemble(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
   for (int i = 0; i < NB; ++i)
-    if (B.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(B, status, i, INLA_E_NOT_SPD);
+    if (B.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(B, status.data(), i, INLA_E_NOT_SPD);
   return INLA_OK;
 }
 
@@ -625,8 +735,34 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     cudaMemcpyAsync(d_perm[mi], models[mi]->perm.data(), sizeof(int32_t) * models[mi]->d.n, cudaMemcpyHostToDevice, st);
   }
   double* d_gather = cfix.take<double>(max_np);
+  const bool share = mixed && !(o.flags & INLA_OPT_NO_SHARED_START);
   for (auto& kv : groups) {
-    const std::vector<int>& idx = kv.second;
+    // Order the group's points: leaders (Newton from x = 0) first, then followers (the later
+    // points of a Poisson model with several points in the group: they start from the first
+    // point's mode and final factor).  anchor_of: the leader slot of each follower slot.
+    std::vector<int> idx;
+    std::vector<int> anchor_of;
+    int nlead = 0;
+    {
+      std::map<int, int> first_of_model;  // model index -> its first point's position in idx
+      std::vector<int> followers;
+      for (int b : kv.second) {
+        const int mi = mi_of[b];
+        const bool poisson = models[mi]->d.likelihood == INLA_LIK_POISSON;
+        if (share && poisson && first_of_model.count(mi)) {
+          followers.push_back(b);
+        } else {
+          if (!first_of_model.count(mi)) first_of_model[mi] = (int)idx.size();
+          idx.push_back(b);
+        }
+      }
+      nlead = (int)idx.size();
+      anchor_of.assign(nlead, -1);
+      for (int b : followers) {
+        idx.push_back(b);
+        anchor_of.push_back(first_of_model[mi_of[b]]);
+      }
+    }
     const int G = (int)idx.size();
     const ModelDev& d0 = models[mi_of[idx[0]]]->d;
     Layout L{d0.n_pad, d0.nd_pad, d0.k_pad, d0.m, S, mixed, want_var};
@@ -672,7 +808,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
         if (Bt.h[g].nd != Bt.h[0].nd) return INLA_E_UNSUPPORTED;
     }
     std::vector<int> status, iters;
-    int rc = run_batch(Bt, mlist, o, want_var, status, iters);
+    int rc = run_batch(Bt, mlist, o, want_var, status, iters, nlead, anchor_of);
     if (rc != INLA_OK) return rc;
     std::vector<double> out;
     std::vector<int32_t> info;

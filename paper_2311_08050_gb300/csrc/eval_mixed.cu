@@ -6,6 +6,7 @@
 // tile columns; 64-wide inner steps in the triangular solves.
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include "df64.cuh"
 #include "mixed.h"
 
@@ -163,7 +164,7 @@ struct NbTune {
   int runs = 0;
   int best = 0;  // 0: undecided
 };
-std::map<std::pair<int, int>, NbTune> g_nb_tune;
+std::map<std::tuple<int, int, int>, NbTune> g_nb_tune;  // (matrix size, slices, slots)
 
 // INLA_OUTER_BLOCK=256 or 512 pins the outer block of every mixed Cholesky (no tuning runs):
 // under a profiler the tuner's timings would not reflect the unprofiled program.
@@ -176,12 +177,12 @@ int pinned_nb() {
   return v;
 }
 
-int pick_nb(const MRef& M, int S, NbTune*& tune, int& cand) {
+int pick_nb(const MRef& M, int S, int nslots, NbTune*& tune, int& cand) {
   tune = nullptr;
   cand = -1;
   if (pinned_nb()) return pinned_nb();
   if (M.n < 2 * kNbCandidates[1]) return kNbCandidates[0];  // too small for the wider panel to matter
-  NbTune& t = g_nb_tune[{M.n, S}];
+  NbTune& t = g_nb_tune[std::make_tuple(M.n, S, nslots)];
   if (t.best) return t.best;
   if (t.runs == 2) {
     float ms[2] = {0.f, 0.f};
@@ -206,15 +207,21 @@ int pick_nb(const MRef& M, int S, NbTune*& tune, int& cand) {
 
 int mixed_nb_choice(int n, int S) {
   if (pinned_nb()) return pinned_nb();
-  auto it = g_nb_tune.find({n, S});
-  return it == g_nb_tune.end() ? 0 : it->second.best;
+  int best = 0, most_slots = -1;  // the decided choice for the largest batch of this size
+  for (const auto& kv : g_nb_tune)
+    if (std::get<0>(kv.first) == n && std::get<1>(kv.first) == S && kv.second.best &&
+        std::get<2>(kv.first) > most_slots) {
+      most_slots = std::get<2>(kv.first);
+      best = kv.second.best;
+    }
+  return best;
 }
 
 int mixed_potrf(Batch& B, int sel) {
   const MRef M = mref(B, sel);
   NbTune* tune = nullptr;
   int cand = -1;
-  const int nb = pick_nb(M, B.S, tune, cand);
+  const int nb = pick_nb(M, B.S, B.n, tune, cand);
   if (tune) {
     // a tuning run: timed, never captured
     for (auto& e : tune->ev[cand])

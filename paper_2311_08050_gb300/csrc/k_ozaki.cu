@@ -730,15 +730,19 @@ struct OzStats {
   int64_t launches = 0;
   double alg_flops = 0.0;     // 2 * (needed output elements) * K, per the tile k-ranges
   double tensor_flops = 0.0;  // alg_flops * S (S + 1) / 2 BF16 passes
+  double alg_bytes = 0.0;     // compulsory DRAM bytes: slice planes once + C written (and read)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
 static OzStats g_stats;
 bool oz_stats_active() { return g_stats.on; }
 
 // Algorithmic flops of a launch: 2 K' per needed output element, K' the tile's k range
-// (lower launches need the elements on or below the diagonal).
-static double oz_alg_flops(const OzArgs& a, int nslots, int bn) {
-  double f = 0.0;
+// (lower launches need the elements on or below the diagonal).  Also its compulsory DRAM
+// bytes: every needed element of the double-float C written once (8 bytes) and, when
+// accumulating, read once; the S BF16 slice planes of both operands read once (2 S (M + N) K
+// bytes; the same operand for A and B is counted once).
+static double oz_alg_flops(const OzArgs& a, int nslots, int bn, bool same_operand, double* bytes) {
+  double f = 0.0, elems_all = 0.0;
   for (int tm = 0; tm < a.tiles_m; ++tm) {
     const int tn_end = a.lower ? std::min(a.tiles_n, (tm + 1) * (OZ_BM / bn)) : a.tiles_n;
     for (int tn = 0; tn < tn_end; ++tn) {
@@ -753,7 +757,13 @@ static double oz_alg_flops(const OzArgs& a, int nslots, int bn) {
       else
         elems = (double)rows * cols;
       f += 2.0 * elems * (a.K - k_lo);
+      elems_all += elems;
     }
+  }
+  if (bytes) {
+    const double c_bytes = elems_all * (a.alpha != 0.f ? 16.0 : 8.0);
+    const double op_bytes = 2.0 * a.S * (double)a.K * (same_operand ? a.M : (double)a.M + a.N);
+    *bytes = (c_bytes + op_bytes) * nslots;
   }
   return f * nslots;
 }
@@ -805,8 +815,10 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args_in, int n
     cudaEventRecord(e1, st);
     g_stats.ev.push_back({e0, e1});
     g_stats.launches += 1;
-    const double f = oz_alg_flops(a, nslots, bn);
+    double by = 0.0;
+    const double f = oz_alg_flops(a, nslots, bn, A.planes == B.planes, &by);
     g_stats.alg_flops += f;
+    g_stats.alg_bytes += by;
     g_stats.tensor_flops += f * a.S * (a.S + 1) / 2;
   }
   return rc;
@@ -841,8 +853,9 @@ extern "C" int inla_test_stats_read(double* out) {
   out[1] = g_stats.alg_flops;
   out[2] = g_stats.tensor_flops;
   out[3] = ms;
+  out[4] = g_stats.alg_bytes;
   g_stats.launches = 0;
-  g_stats.alg_flops = g_stats.tensor_flops = 0.0;
+  g_stats.alg_flops = g_stats.tensor_flops = g_stats.alg_bytes = 0.0;
   return INLA_OK;
 }
 

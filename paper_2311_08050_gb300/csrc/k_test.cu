@@ -1,4 +1,5 @@
 // Test hooks (include/inla_testing.h): isolated runs of the mixed-precision building blocks.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 #include "../../include/inla_testing.h"
@@ -220,5 +221,57 @@ extern "C" int inla_test_trsv_df(const double* L, const double* b, int32_t n, in
   cudaFree(err);
   cudaFree(info);
   if (rc == INLA_E_CUDA) cudaGetLastError();
+  return rc;
+}
+
+// ---- arithmetic peak probes (FMA throughput of the FP64 and FP32 pipes) ----
+namespace inla {
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* sink, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i) * (T)1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);  // eight independent chains per thread
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == (T)-1.2345) sink[0] = s;  // never true for these inputs; keeps the chains live
+}
+}  // namespace inla
+
+// Best-of-`reps` FMA throughput in TFLOP/s (2 flops per FMA) of the FP64 (kind 0) or FP32
+// (kind 1) pipes over every SM of the current device, timed with CUDA events.
+extern "C" int inla_test_fma_peak(int32_t kind, int32_t reps, double* tflops) {
+  if (!tflops || (kind != 0 && kind != 1) || reps <= 0) return INLA_E_BADARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return INLA_E_CUDA;
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, 16) != cudaSuccess) return INLA_E_NOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256;
+  const int iters = kind == 0 ? 2048 : 65536;
+  double best = 0.0;
+  int rc = INLA_OK;
+  for (int r = 0; r < reps + 1 && rc == INLA_OK; ++r) {  // first run: warm-up
+    cudaEventRecord(e0);
+    if (kind == 0) k_fma_probe<double><<<blocks, threads>>>((double*)sink, iters, 0.9999999, 1e-7);
+    else k_fma_probe<float><<<blocks, threads>>>((float*)sink, iters, 0.9999f, 1e-4f);
+    cudaEventRecord(e1);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = INLA_E_CUDA;
+    const double fl = 2.0 * 8.0 * iters * (double)threads * blocks;
+    if (r > 0 && ms > 0.f) best = std::max(best, fl / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (rc != INLA_OK) cudaGetLastError();
+  *tflops = best;
   return rc;
 }

@@ -22,6 +22,7 @@ FACTOR = {"icar": 0, "rw1": 1, "rw2": 2, "iid": 3}
 PRIOR = {"gauss": 0, "pc_prec": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 OPT_DEVICE_OUT = 1
+OPT_NO_SHARED_START = 2
 
 EXPORTED = ["inla_opts_default", "inla_model_create", "inla_model_destroy", "inla_eval_theta",
             "inla_eval_batch", "inla_marginals", "inla_status_string"]
@@ -94,7 +95,7 @@ def _ptr(a, ct):
 
 
 def make_opts(precision="fp64", slices=0, newton_tol=1e-8, newton_max=50, stream=None, device_out=False,
-              spin_limit=1 << 26, newton_slices=0):
+              spin_limit=1 << 26, newton_slices=0, flags_extra=0):
     o = Opts()
     lib().inla_opts_default(C.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -104,7 +105,7 @@ def make_opts(precision="fp64", slices=0, newton_tol=1e-8, newton_max=50, stream
     o.newton_max = newton_max
     o.spin_limit = spin_limit
     o.stream = stream
-    o.flags = OPT_DEVICE_OUT if device_out else 0
+    o.flags = (OPT_DEVICE_OUT if device_out else 0) | int(flags_extra)
     return o
 
 

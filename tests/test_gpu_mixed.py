@@ -235,3 +235,35 @@ def test_outer_block_tuner_decides_and_results_agree():
     assert L.inla_test_outer_block(n_pad, 4) in (256, 512)
     assert L.inla_test_outer_block(n_pad, 5) in (256, 512)
 
+
+
+def _fresh_factors():
+    import ctypes as C
+    L = inla.lib()
+    L.inla_test_newton_trace.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_int32]
+    steps = np.zeros(256)
+    ref = np.zeros(256, dtype=np.int32)
+    n = L.inla_test_newton_trace(steps.ctypes.data_as(C.POINTER(C.c_double)), ref.ctypes.data_as(C.POINTER(C.c_int32)), 256)
+    return int(ref[:n].sum()), n
+
+
+def test_fd_batch_followers_start_from_the_centre_mode():
+    """A 5-point central FD stencil on one Poisson model: the centre runs Newton from 0, the
+    four other points start from its mode with its final factor.  Every point still matches the
+    oracle at the mixed tolerances, and the batch needs fewer Newton factorisations than with
+    every point on its own (INLA_OPT_NO_SHARED_START)."""
+    spec = synth.spatial_poisson("fd_n1024", synth.SEED_BASE + 81, 1023, 4000, [0.0, np.log(0.2)])
+    thetas = synth._fd_batch(np.array([0.1, np.log(0.25)]))
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
+    shared_factors, shared_iters = _fresh_factors()
+    _check(spec, thetas, lp, st, xs, vs)
+    lp0, st0, xs0, vs0 = inla.eval_batch([m], thetas, precision="mixed", flags_extra=inla.OPT_NO_SHARED_START)
+    own_factors, own_iters = _fresh_factors()
+    _check(spec, thetas, lp0, st0, xs0, vs0)
+    print(f"Newton factorisations: shared start {shared_factors} ({shared_iters} iterations), "
+          f"own {own_factors} ({own_iters} iterations)")
+    assert shared_factors < own_factors
+    # both routes converge to the same modes (step tolerance 1e-8)
+    for b in range(len(thetas)):
+        assert np.max(np.abs(xs[b] - xs0[b])) <= 1e-6 * max(1.0, np.max(np.abs(xs0[b])))
