@@ -184,7 +184,8 @@ def run_ours(args):
     xp = [xbuf[b].data_ptr() for b in range(nb)]
     vp = [vbuf[b].data_ptr() for b in range(nb)]
     kw = dict(precision=args.precision, slices=args.slices, newton_slices=args.newton_slices, stream=sptr,
-              device_out=True, x_out=xp, var_out=vp)
+              device_out=True, x_out=xp, var_out=vp, prior_slices=args.prior_slices, reuse_below=args.reuse_below,
+              reuse_shrink=args.reuse_shrink)
 
     def step():
         lp, st, _, _ = inla.eval_batch([model], thetas, **kw)
@@ -227,6 +228,12 @@ def run_ours(args):
     L.inla_test_stats_read(stats)
     pbuf = C.create_string_buffer(1 << 16)
     L.inla_test_profile_read(pbuf, 1 << 16)
+    phbuf = C.create_string_buffer(1 << 12)
+    L.inla_test_phase_read(phbuf, 1 << 12)
+    phases = []
+    for line in phbuf.value.decode().splitlines():
+        name, cnt, tot = line.split()
+        phases.append({"phase": name, "ms": round(float(tot), 3)})
     breakdown = []
     for line in pbuf.value.decode().splitlines():
         name, cnt, tot = line.split()
@@ -277,12 +284,14 @@ def run_ours(args):
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
            "config": {"workload": args.workload, "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
-                      "precision": args.precision, "slices": args.slices,
+                      "precision": args.precision, "slices": args.slices, "newton_slices": args.newton_slices,
+                      "prior_slices": args.prior_slices or args.slices,
+                      "reuse_below": args.reuse_below or 1e-2, "reuse_shrink": args.reuse_shrink or 0.25,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "outer_block_tuned": outer_block,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
            "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
-           "kernel_breakdown": breakdown[:12]}
+           "kernel_breakdown": breakdown[:12], "phase_breakdown": phases}
     # ---------------- end to end from host buffers ----------------
     if not args.no_e2e:
         from paper_2311_08050_gb300.synth import ModelSpec  # noqa: F401
@@ -394,6 +403,11 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--slices", type=int, default=5, help="slices of the prior inversion and the factor at the mode")
     ap.add_argument("--newton-slices", type=int, default=4, help="slices of the Newton-step factorisations")
+    ap.add_argument("--prior-slices", type=int, default=0, help="slices of the prior inversion (0: --slices)")
+    ap.add_argument("--reuse-below", type=float, default=0.0, help="modified Newton: reuse a factor once steps are "
+                    "below this (0: library default)")
+    ap.add_argument("--reuse-shrink", type=float, default=0.0, help="modified Newton: keep a factor while steps "
+                    "shrink at least by this ratio (0: library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -119,6 +119,12 @@ typedef struct {
   int64_t spin_limit;  /* iteration limit of every device-side wait (default 1<<26) */
   void *stream;        /* cudaStream_t to run on, or NULL for the default stream */
   int32_t flags;       /* INLA_OPT_* */
+  int32_t prior_slices;  /* INLA_MIXED: slices of the prior covariance factorisation and inverse;
+                          0 = `slices` */
+  double reuse_below;  /* INLA_MIXED modified Newton: a factor may be kept for later iterations
+                          once the step (infinity norm) is below this; 0 = default (1e-2) */
+  double reuse_shrink; /* ... and is kept while every step is at most this fraction of the one
+                          before; 0 = default (0.25) */
 } inla_opts;
 
 typedef struct inla_model inla_model;   /* opaque; owns device copies of the model */

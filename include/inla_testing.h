@@ -52,6 +52,11 @@ int64_t inla_test_launch_count(void);
  * (largest total first) into buf and resets; it returns the bytes written. */
 void inla_test_profile_enable(int on);
 int inla_test_profile_read(char *buf, int len);
+/* Phase profile of the same recording: "name count total_ms" lines in order of first appearance
+ * for the phases of a batch (prior, Newton of the leading points, their factor at the mode,
+ * Newton of the points that start from another point's mode, their factor, and the
+ * log-determinants, variances and log pi~); resets and returns the bytes written. */
+int inla_test_phase_read(char *buf, int len);
 
 /* Dense covariance entries sigma2 * exp(-sqrt((dx * inv_rx)^2 + (dy * inv_ry)^2)) for n <= 8192
  * host points (row-major n x 2), computed by the mixed path's double-float device code (its own

@@ -287,13 +287,47 @@ static void set_factor_ptrs(Slot& dst, const Slot& src) {
 // shrink at least 4x per iteration (modified Newton: the gradient is exact, so the fixed point
 // is still the mode); `own` then holds their own matrix pointers, restored before the first
 // factorisation of their own.
+// wls_start: the slots start instead from the solution of a weighted least-squares system
+// Q_p + A^T W A (Poisson: W = diag(y + 1/2) with the working response log(y + 1/2) - offset;
+// Gaussian: its exact Newton system) -- one factorisation, kept as the first iterations'
+// factor while it serves (start_shared), which near the mode approximates the Hessian
+// A^T diag(exp(eta)) A + Q_p well: fewer Newton factorisations than from x = 0.
 static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts& o, int* status, int* iters,
-                        int* converged, int* d_flags, bool start_shared, const std::vector<Slot>& own) {
+                        int* converged, int* d_flags, bool start_shared, const std::vector<Slot>& own,
+                        bool wls_start = false) {
   const int NB = V.n;
   std::vector<double> out;
   std::vector<int32_t> info;
   V.S = V.S_newton;
   if (!start_shared) launch_zero_vec(V.d_slots, NB, 0, V.max_n, V.st);
+  if (wls_start) {
+    launch_wls_start(V.d_slots, NB, V.max_m, V.max_n, V.st);
+    op_assemble_q(V);
+    launch_gradient(V.d_slots, NB, V.max_n, V.st);
+    INLA_TRY(op_potrf(V, SEL_L));
+    INLA_TRY(solve_llt(V, SEL_L, V_G, V_T2, V_G));
+    launch_newton_xu(V.d_slots, NB, V.max_n, V.st);  // xn = 0 + g
+    if (V.max_k > 0) {
+      INLA_TRY(op_schur(V));
+      launch_cx(V.d_slots, NB, V.max_k, V.st);
+      INLA_TRY(solve_llt(V, SEL_S, V_KV1, V_KV2, V_KV1));
+      if (V.mixed) launch_z_gemv_df(V.d_slots, NB, V.max_n, V.st);
+      else launch_z_gemv(V.d_slots, NB, V.max_n, V.st);
+      INLA_TRY(solve_lt(V, SEL_L, V_T2, V_G));
+      launch_krige_apply(V.d_slots, NB, V.max_n, V.st);
+    }
+    launch_step_norm(V.d_slots, NB, V.max_n, V.st);
+    launch_accept(V.d_slots, NB, V.max_n, V.st);
+    INLA_TRY(read_outputs(V, out, info));
+    double mx = 0.0;
+    for (int i = 0; i < NB; ++i) {
+      if (V.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(V, status, i, INLA_E_NOT_SPD);
+      if (V.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
+    }
+    g_newton_trace.push_back({mx, 1});
+    sync_active(V);
+    start_shared = true;  // the start system's factor serves the first iterations
+  }
   launch_eval_lik(V.d_slots, NB, 0, V.max_m, V.st);
   op_qp_gemv(V, 0);
   INLA_TRY(read_outputs(V, out, info));
@@ -325,7 +359,7 @@ static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts
         it_own = it;
       }
     } else {
-      refactor = !V.mixed || it - it_own < 2 || last_step > 1e-2 || !reuse_ok;
+      refactor = !V.mixed || it - it_own < 2 || last_step > o.reuse_below || !reuse_ok;
     }
     if (refactor) op_assemble_q(V);
     launch_gradient(V.d_slots, NB, V.max_n, V.st);
@@ -374,7 +408,7 @@ static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts
       double mx = 0.0;
       for (int i = 0; i < NB; ++i)
         if (V.h[i].active) mx = std::max(mx, out[(size_t)i * SLOT_NOUT + OUT_STEP]);
-      reuse_ok = (refactor && !shared) || mx < 0.25 * last_step;
+      reuse_ok = (refactor && !shared) || mx < o.reuse_shrink * last_step;
       last_step = mx;
       g_newton_trace.push_back({mx, refactor ? 1 : 0});
     }
@@ -436,7 +470,8 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   }
   sync_active(B);
   // ---------------- prior precision ----------------
-  B.S = B.S_exact;
+  prof_phase("prior");
+  B.S = B.S_prior;
   launch_theta_prior(B.d_slots, NB, B.st);
   for (int i = 0; i < NB; ++i) cudaMemsetAsync(B.h[i].Qp, 0, (size_t)B.h[i].n_pad * B.h[i].n_pad * 8, B.st);
   INLA_TRY(debug_check(B.st, "prior start"));
@@ -456,10 +491,12 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   g_newton_trace.clear();
   int rc = INLA_OK;
   // ---------------- Newton, leaders ----------------
+  prof_phase("newton_lead");
   {
     Batch V = view_of(B, 0, nlead);
     std::vector<Slot> own(V.h);
-    rc = newton_phase(V, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, false, own);
+    rc = newton_phase(V, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, false, own,
+                      V.mixed && !(o.flags & INLA_OPT_NO_SHARED_START));
     copy_back(B, V, 0);
   }
   // a point that failed or did not converge leaves the rest of the evaluation
@@ -472,6 +509,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   if (rc == INLA_OK) settle(0, nlead);
   // ---------------- factor at the leaders' modes; followers from their anchors ----------------
   if (rc == INLA_OK && nlead < NB) {
+    prof_phase("factor_lead");
     Batch V = view_of(B, 0, nlead);
     rc = final_factor(V);
     copy_back(B, V, 0);
@@ -490,23 +528,27 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
         }
       }
       sync_active(F);
+      prof_phase("newton_follow");
       rc = newton_phase(F, models.data() + nlead, o, status.data() + nlead, iters.data() + nlead,
                         converged.data() + nlead, d_flags, anchors_ok, own);
       copy_back(B, F, nlead);
       if (rc == INLA_OK) {
         settle(nlead, NB);
+        prof_phase("factor_follow");
         Batch G = view_of(B, nlead, NB);
         rc = final_factor(G);
         copy_back(B, G, nlead);
       }
     }
   } else if (rc == INLA_OK) {
+    prof_phase("factor_lead");
     rc = final_factor(B);
   }
   cudaFreeAsync(d_flags, B.st);
   if (rc != INLA_OK) return rc;
   sync_active(B);
   // ---------------- at the modes: log-determinants, variances, log pi~ ----------------
+  prof_phase("logdet_variances");
   B.S = B.S_exact;
   op_logdet(B, SEL_L, OUT_LOGDET_Q);
   if (B.max_k > 0) op_logdet(B, SEL_S, OUT_LOGDET_S);
@@ -669,12 +711,18 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   if (o.newton_tol <= 0) o.newton_tol = 1e-8;
   if (o.newton_max <= 0) o.newton_max = 50;
   if (o.spin_limit <= 0) o.spin_limit = (int64_t)1 << 26;
+  if (!(o.reuse_below > 0)) o.reuse_below = 1e-2;
+  if (!(o.reuse_shrink > 0)) o.reuse_shrink = 0.25;
+  if (o.reuse_shrink >= 1.0) return INLA_E_BADARG;
   if (o.precision != INLA_FP64 && o.precision != INLA_MIXED) return INLA_E_BADARG;
   const bool mixed = o.precision == INLA_MIXED;
   const int S_exact = mixed ? (o.slices == 0 ? 5 : o.slices) : 0;
   const int S_newton = mixed ? (o.newton_slices == 0 ? std::min(4, S_exact) : o.newton_slices) : 0;
-  if (mixed && (S_exact < 2 || S_exact > OZ_MAX_S || S_newton < 2 || S_newton > OZ_MAX_S)) return INLA_E_BADARG;
-  const int S = std::max(S_exact, S_newton);  // workspace capacity
+  const int S_prior = mixed ? (o.prior_slices == 0 ? S_exact : o.prior_slices) : 0;
+  if (mixed && (S_exact < 2 || S_exact > OZ_MAX_S || S_newton < 2 || S_newton > OZ_MAX_S || S_prior < 2 ||
+                S_prior > OZ_MAX_S))
+    return INLA_E_BADARG;
+  const int S = std::max(std::max(S_exact, S_newton), S_prior);  // workspace capacity
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
@@ -775,6 +823,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     Bt.spin_limit = o.spin_limit;
     Bt.S_exact = S_exact;
     Bt.S_newton = S_newton;
+    Bt.S_prior = S_prior;
     Bt.max_t = d0.n_pad / TB;
     Bt.max_td = d0.nd_pad / TB;
     Bt.max_tk = d0.k_pad / TB;
@@ -858,6 +907,8 @@ extern "C" int inla_opts_default(inla_opts* o) {
   o->newton_tol = 1e-8;
   o->newton_max = 50;
   o->spin_limit = (int64_t)1 << 26;
+  o->reuse_below = 1e-2;
+  o->reuse_shrink = 0.25;
   o->stream = nullptr;
   o->flags = 0;
   return INLA_OK;

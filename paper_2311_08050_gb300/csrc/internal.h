@@ -171,6 +171,7 @@ extern int64_t g_kernel_launches;
 // event on the profiled stream so that per-kernel times can be attributed (prof.cu)
 int count_launch(const char* name);
 void prof_set_stream(cudaStream_t st);
+void prof_phase(const char* name);  // while the profiler is on: a phase boundary of a batch
 bool prof_active();          // the per-kernel event profiler is recording
 bool oz_stats_active();      // the GEMM launch statistics are recording
 }  // namespace inla

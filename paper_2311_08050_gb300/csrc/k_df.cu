@@ -191,118 +191,167 @@ __global__ void k_s_pad_identity(Slot* slots) {
 }
 
 // Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
-// GPU's FP64 rate is ~2 FMA/clock/SM).  Register-blocked: thread (ty, tx) of a 16 x 16 grid
-// owns the 16 elements (ty + 16 bi, tx + 16 bc) of the tile and of Y; each of the 64 steps
-// broadcasts one column of A and one row of Y through double-buffered shared arrays, one
-// barrier per step.  Augmented right-looking elimination on [A | Y = I]: step j subtracts
-// u_i = a_ij / a_jj times row j from every row i > j, i.e. a_ic -= u_i a_cj (j < c <= i) and
-// Y_ic -= u_i Y_jc (c <= j).  Then A = L_1 D L_1^T with L_1 = unit lower and Y = L_1^-1, so
-// L_ij = a_ij / sqrt(a_jj) and L^-1 = D^-1/2 Y: (L^-1)_ic = Y_ic / L_ii.  Stores the factor
-// tile (double-float, upper part zeroed) and the inverse tile (double-float, in the FP64-sized
-// cells of the inverse-tile array).
-__global__ void __launch_bounds__(256) k_potrf_diag_df(Slot* slots, int sel, int kt) {
+// GPU's FP64 rate is ~2 FMA/clock/SM).  One CTA of 1024 threads per tile, the tile in shared
+// memory (row pitch 65 cells).  Factor: right-looking elimination A = L1 D L1^T, step j
+// subtracting (a_ij / a_jj) a_cj from every a_ic with i >= c > j.  The elements of step j are the
+// first (63 - j)(64 - j) / 2 entries of a fixed table that lists the lower triangle by column,
+// last column first, so the threads share each step evenly (at most two elements each, skipped
+// uniformly when absent); thread 0 only updates the next pivot a_{j+1,j+1} and publishes its
+// reciprocal, so one barrier per step closes it.  Then L = L1 D^1/2 is written out and L1 is
+// inverted in place by levels (s = 1, 2, .., 32: two inverted diagonal blocks of size s and the
+// block below them give the inverse of the 2s block, -Y22 L21 Y11), so L^-1 = D^-1/2 Y.  Stores
+// the factor tile (double-float, upper part zeroed) and the inverse tile (double-float, in the
+// FP64-sized cells of the inverse-tile array).
+constexpr int DG_LD = TB + 1;
+constexpr int DG_THREADS = 1024;
+__device__ __forceinline__ df dg_ld(const float2* t, int i, int c) { return df_make(t[i * DG_LD + c].x, t[i * DG_LD + c].y); }
+__device__ __forceinline__ void dg_st(float2* t, int i, int c, df v) { t[i * DG_LD + c] = make_float2(v.hi, v.lo); }
+
+__global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int sel, int kt) {
   const Slot& s = slots[blockIdx.x];
   if (!s.active) return;
   DfRef M = df_ref(s, sel);
   if (kt * TB >= M.n) return;
-  __shared__ float2 colb[2][TB], rowb[2][TB], rpb[2];
-  __shared__ float2 dsq[TB], rdq[TB];
+  constexpr int NTRI = TB * (TB + 1) / 2;  // 2080 lower-triangle elements (diagonal included)
+  constexpr int NW = DG_THREADS - 1;       // threads sharing the elements of a step
+  __shared__ float2 t[TB * DG_LD];
+  __shared__ uint16_t tab[NTRI];           // (i << 8) | c, columns 63, 62, .., 0, rows ascending
+  __shared__ float2 rpa[TB];               // 1 / a_jj
+  __shared__ float2 dsq[TB], rdq[TB];      // sqrt(a_jj), 1 / sqrt(a_jj)
+  __shared__ int bad_sh;
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
   float2* base = M.A + (size_t)kt * TB * M.ld + (size_t)kt * TB;
-  df A[4][4];
-#pragma unroll
-  for (int bi = 0; bi < 4; ++bi)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) {
-      const float2 v = base[(size_t)(ty + 16 * bi) * M.ld + tx + 16 * bc];
-      A[bi][bc] = df_make(v.x, v.y);
-    }
-  // Y: the same row operations applied to the identity (augmented elimination), which ends as
-  // the inverse of the unit lower factor; Linv = D^-1/2 Y below.
-  df Y[4][4];
-#pragma unroll
-  for (int bi = 0; bi < 4; ++bi)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) Y[bi][bc] = df_make((ty + 16 * bi) == (tx + 16 * bc) ? 1.f : 0.f, 0.f);
-  bool bad = false;
-  // ---- factor: step j subtracts (a_ij / a_jj) row j from every row i > j of [A | Y] ----
-#pragma unroll
-  for (int bj = 0; bj < 4; ++bj) {
-    for (int jj = 0; jj < 16; ++jj) {
-      const int j = bj * 16 + jj, buf = j & 1;
-      if (ty == jj) {
-        // row j of Y is final (no later step reaches it); its nonzeros are columns c <= j
-#pragma unroll
-        for (int bc = 0; bc <= bj; ++bc) rowb[buf][tx + 16 * bc] = make_float2(Y[bj][bc].hi, Y[bj][bc].lo);
-      }
-      if (tx == jj) {
-#pragma unroll
-        for (int bi = bj; bi < 4; ++bi) colb[buf][ty + 16 * bi] = make_float2(A[bi][bj].hi, A[bi][bj].lo);
-        if (ty == jj) {
-          df p = A[bj][bj];
-          if (!(p.hi > 0.f) || !isfinite(p.hi)) {
-            bad = true;
-            atomicMin(&s.info[1], kt * TB + j);
-            p = df_make(1.f, 0.f);
-          }
-          const df rp = df_recip(p);
-          rpb[buf] = make_float2(rp.hi, rp.lo);
-        }
-      }
-      __syncthreads();
-      const df rp = df_make(rpb[buf].x, rpb[buf].y);
-#pragma unroll
-      for (int bi = bj; bi < 4; ++bi) {
-        const int i = ty + 16 * bi;
-        if (i > j) {
-          const df u = df_mul(df_make(colb[buf][i].x, colb[buf][i].y), rp);
-#pragma unroll
-          for (int bc = bj; bc <= bi; ++bc) {
-            const int c = tx + 16 * bc;
-            if (c > j && c <= i) A[bi][bc] = df_add_fast(A[bi][bc], df_neg(df_mul(u, df_make(colb[buf][c].x, colb[buf][c].y))));
-          }
-#pragma unroll
-          for (int bc = 0; bc <= bj; ++bc) {
-            const int c = tx + 16 * bc;
-            if (c <= j) Y[bi][bc] = df_add_fast(Y[bi][bc], df_neg(df_mul(u, df_make(rowb[buf][c].x, rowb[buf][c].y))));
-          }
-        }
-      }
-    }
+  if (tid == 0) bad_sh = 0;
+  for (int e = tid; e < TB * TB; e += DG_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    if (c <= i) t[i * DG_LD + c] = base[(size_t)i * M.ld + c];
   }
-  if (bad) atomicOr(&s.info[0], INFO_NOT_SPD);
-  // ---- scaling: L_jj = sqrt(a_jj), L_ij = a_ij / L_jj ----
-  if (tx == ty) {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      df p = A[b][b];
-      if (!(p.hi > 0.f) || !isfinite(p.hi)) p = df_make(1.f, 0.f);
-      const df d = df_sqrt(p), rd = df_recip(d);
-      dsq[tx + 16 * b] = make_float2(d.hi, d.lo);
-      rdq[tx + 16 * b] = make_float2(rd.hi, rd.lo);
+  // table: column c (from 63 down) occupies positions [ (63-c)(64-c)/2, (64-c)(65-c)/2 )
+  for (int x = tid; x < TB * TB; x += DG_THREADS) {
+    const int c = x >> 6, i = x & 63;
+    if (i >= c) {
+      const int w = 63 - c;
+      tab[w * (w + 1) / 2 + (i - c)] = (uint16_t)((i << 8) | c);
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int bi = 0; bi < 4; ++bi)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) {
-      const int i = ty + 16 * bi, c = tx + 16 * bc;
-      if (c < i) A[bi][bc] = df_mul(A[bi][bc], df_make(rdq[c].x, rdq[c].y));
-      else if (c == i) A[bi][bc] = df_make(dsq[i].x, dsq[i].y);
-      else A[bi][bc] = df_make(0.f, 0.f);
+  auto pivot_recip = [&](df p, int j) {
+    if (!(p.hi > 0.f) || !isfinite(p.hi)) {
+      bad_sh = 1;
+      atomicMin(&s.info[1], kt * TB + j);
+      p = df_make(1.f, 0.f);
     }
+    const df r = df_recip(p);
+    rpa[j] = make_float2(r.hi, r.lo);
+  };
+  if (tid == 0) pivot_recip(dg_ld(t, 0, 0), 0);
+  __syncthreads();
+  // ---- factor: 63 elimination steps, one barrier each ----
+  for (int j = 0; j < TB - 1; ++j) {
+    const df r = df_make(rpa[j].x, rpa[j].y);
+    const int w = TB - 1 - j;              // columns j+1 .. 63: w of them
+    const int cnt = w * (w + 1) / 2;
+    const int pidx = cnt - w;              // position of (j+1, j+1): first of column j+1
+    if (tid == 0) {
+      const df aij = dg_ld(t, j + 1, j);
+      const df v = df_add_fast(dg_ld(t, j + 1, j + 1), df_neg(df_mul(df_mul(aij, r), aij)));
+      dg_st(t, j + 1, j + 1, v);
+      pivot_recip(v, j + 1);
+    } else {
+      // elements (tid - 1) and (tid - 1) + NW of the step's list without its pivot
+      int e0 = tid - 1, e1 = tid - 1 + NW;
+      e0 += e0 >= pidx;
+      e1 += e1 >= pidx;
+      const bool h0 = e0 < cnt, h1 = e1 < cnt;
+      df a0, u0, b0, a1, u1, b1;
+      int p0 = 0, p1 = 0;
+      if (h0) {
+        const int ic = tab[e0], i = ic >> 8, c = ic & 255;
+        p0 = i * DG_LD + c;
+        a0 = dg_ld(t, i, c);
+        u0 = dg_ld(t, i, j);
+        b0 = dg_ld(t, c, j);
+      }
+      if (h1) {
+        const int ic = tab[e1], i = ic >> 8, c = ic & 255;
+        p1 = i * DG_LD + c;
+        a1 = dg_ld(t, i, c);
+        u1 = dg_ld(t, i, j);
+        b1 = dg_ld(t, c, j);
+      }
+      if (h0) {
+        const df v = df_add_fast(a0, df_neg(df_mul(df_mul(u0, r), b0)));
+        t[p0] = make_float2(v.hi, v.lo);
+      }
+      if (h1) {
+        const df v = df_add_fast(a1, df_neg(df_mul(df_mul(u1, r), b1)));
+        t[p1] = make_float2(v.hi, v.lo);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad_sh && tid == 0) atomicOr(&s.info[0], INFO_NOT_SPD);
+  // ---- unit factor L1 (in place below the diagonal), sqrt of the pivots ----
+  if (tid < TB) {
+    df p = dg_ld(t, tid, tid);
+    if (!(p.hi > 0.f) || !isfinite(p.hi)) p = df_make(1.f, 0.f);
+    const df d = df_sqrt(p), rd = df_recip(d);
+    dsq[tid] = make_float2(d.hi, d.lo);
+    rdq[tid] = make_float2(rd.hi, rd.lo);
+  }
+  for (int e = tid; e < TB * TB; e += DG_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    if (i > c) dg_st(t, i, c, df_mul(dg_ld(t, i, c), df_make(rpa[c].x, rpa[c].y)));
+  }
+  __syncthreads();
+  // ---- L = L1 D^1/2 to global (upper part zeroed) ----
+  for (int e = tid; e < TB * TB; e += DG_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    df v = df_make(0.f, 0.f);
+    if (c < i) v = df_mul(dg_ld(t, i, c), df_make(dsq[c].x, dsq[c].y));
+    else if (c == i) v = df_make(dsq[i].x, dsq[i].y);
+    base[(size_t)i * M.ld + c] = make_float2(v.hi, v.lo);
+  }
+  // ---- Y = L1^-1 in place, level by level (unit diagonal implicit); one output per thread:
+  // level s has 64 / (2 s) blocks of s x s outputs, 32 s in all ----
+  for (int sz = 1; sz < TB; sz <<= 1) {
+    const int lg = __ffs(sz) - 1;          // sz = 2^lg
+    const bool on = tid < 32 * sz;
+    int row = 0, p = 0, c = 0, r = 0;
+    if (on) {
+      const int blk = tid >> (2 * lg), rem = tid & (sz * sz - 1);
+      r = rem >> lg;
+      c = rem & (sz - 1);
+      p = blk * 2 * sz;
+      row = p + sz + r;
+    }
+    df tv;
+    // T = L21 Y11: T_rc = L21_rc + sum_{k = c+1}^{sz-1} L21_rk Y11_kc
+    if (on) {
+      tv = dg_ld(t, row, p + c);
+      for (int k = c + 1; k < sz; ++k) tv = df_add_fast(tv, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
+    }
+    __syncthreads();
+    if (on) dg_st(t, row, p + c, tv);
+    __syncthreads();
+    // Y21 = -Y22 T: -(T_rc + sum_{k < r} Y22_rk T_kc)
+    if (on) {
+      tv = dg_ld(t, row, p + c);
+      for (int k = 0; k < r; ++k) tv = df_add_fast(tv, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
+    }
+    __syncthreads();
+    if (on) dg_st(t, row, p + c, df_neg(tv));
+    __syncthreads();
+  }
+  // ---- L^-1 = D^-1/2 Y ----
   float2* linv = reinterpret_cast<float2*>(M.Linv) + (size_t)kt * TB * TB;
-#pragma unroll
-  for (int bi = 0; bi < 4; ++bi)
-#pragma unroll
-    for (int bc = 0; bc < 4; ++bc) {
-      const int i = ty + 16 * bi, c = tx + 16 * bc;
-      base[(size_t)i * M.ld + c] = make_float2(A[bi][bc].hi, A[bi][bc].lo);
-      const df x = c <= i ? df_mul(Y[bi][bc], df_make(rdq[i].x, rdq[i].y)) : df_make(0.f, 0.f);
-      linv[i * TB + c] = make_float2(x.hi, x.lo);
-    }
+  for (int e = tid; e < TB * TB; e += DG_THREADS) {
+    const int i = e >> 6, c = e & 63;
+    df v = df_make(0.f, 0.f);
+    if (c < i) v = df_mul(dg_ld(t, i, c), df_make(rdq[i].x, rdq[i].y));
+    else if (c == i) v = df_make(rdq[i].x, rdq[i].y);
+    linv[i * TB + c] = make_float2(v.hi, v.lo);
+  }
 }
 
 // Triangular solves with the double-float factor, one cooperative launch per solve:
@@ -542,7 +591,7 @@ void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st) 
   count_launch("k_s_pad_identity"), k_s_pad_identity<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
 void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st) {
-  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, 256, 0, st>>>(slots, sel, kt);
+  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, DG_THREADS, 0, st>>>(slots, sel, kt);
 }
 int launch_trsv_df(const TrsvArgs& a, cudaStream_t st) {
   // resident blocks per SM and SM count, per device (the cooperative grid must fit at once)

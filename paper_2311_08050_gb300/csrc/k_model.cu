@@ -260,6 +260,32 @@ __global__ void __launch_bounds__(256) k_gradient(Slot* slots) {
   }
 }
 
+// Start system of the mixed path's Newton iteration: likelihood weights and residual of a
+// weighted least-squares fit of the linear predictor to pseudo-data (Poisson: weights y + 1/2,
+// targets log(y + 1/2) - offset, the log link's working response with counts shifted off zero;
+// Gaussian: its own weights tau and data, so the start is its exact mode): w = weights,
+// r (held in eta) = weights * targets, and t1 = 0, so that the gradient kernel forms A^T r.
+__global__ void __launch_bounds__(256) k_wls_start(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const ModelDev& md = *s.md;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < s.m; i += gridDim.x * 256) {
+    const double o = md.offset ? md.offset[i] : 0.0;
+    const double y = md.y[i];
+    double w, z;
+    if (md.likelihood == INLA_LIK_POISSON) {
+      w = y + 0.5;
+      z = log(w) - o;
+    } else {
+      w = md.lik_prec;
+      z = y - o;
+    }
+    s.w[i] = w;
+    s.eta[i] = w * z;
+  }
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < s.n_pad; j += gridDim.x * 256) s.t1[j] = 0.0;
+}
+
 __global__ void __launch_bounds__(256) k_newton_xu(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
@@ -397,6 +423,9 @@ void launch_qp_gemv(Slot* slots, int nslots, int which, int max_n, cudaStream_t 
 void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st) { count_launch("k_quad"), k_quad<<<nslots, 256, 0, st>>>(slots, which); }
 void launch_gradient(Slot* slots, int nslots, int max_n, cudaStream_t st) {
   count_launch("k_gradient"), k_gradient<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
+}
+void launch_wls_start(Slot* slots, int nslots, int max_m, int max_n, cudaStream_t st) {
+  count_launch("k_wls_start"), k_wls_start<<<dim3(vgrid(std::max(max_m, max_n)), nslots), 256, 0, st>>>(slots);
 }
 void launch_newton_xu(Slot* slots, int nslots, int max_n, cudaStream_t st) {
   count_launch("k_newton_xu"), k_newton_xu<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots);

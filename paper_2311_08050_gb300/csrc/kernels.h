@@ -55,6 +55,8 @@ void launch_qp_gemv(Slot* slots, int nslots, int which, int max_n, cudaStream_t 
 void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st);
 // g = A^T r - t1   (r held in eta)
 void launch_gradient(Slot* slots, int nslots, int max_n, cudaStream_t st);
+// w, r (in eta) of the weighted least-squares start system, t1 = 0 (mixed Newton's start)
+void launch_wls_start(Slot* slots, int nslots, int max_m, int max_n, cudaStream_t st);
 // xn = x + g ; kv1 = C xn (if k > 0)
 void launch_newton_xu(Slot* slots, int nslots, int max_n, cudaStream_t st);
 void launch_cx(Slot* slots, int nslots, int max_k, cudaStream_t st);

@@ -17,6 +17,7 @@ struct Prof {
   bool on = false;
   cudaStream_t st = nullptr;
   std::vector<std::pair<cudaEvent_t, const char*>> ev;
+  std::vector<std::pair<cudaEvent_t, const char*>> phases;  // phase boundaries of a batch
 };
 Prof g_prof;
 }  // namespace
@@ -36,9 +37,52 @@ int count_launch(const char* name) {
   return 0;
 }
 
+void prof_phase(const char* name) {
+  if (!g_prof.on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) == cudaSuccess) {
+    cudaEventRecord(e, g_prof.st);
+    g_prof.phases.push_back({e, name});
+  }
+}
+
 }  // namespace inla
 
 using namespace inla;
+
+// Writes "name count total_ms\n" lines, in order of first appearance, for the phases of the
+// batches run while the profiler was on (a phase lasts until the next phase mark or the read).
+extern "C" int inla_test_phase_read(char* buf, int len) {
+  if (!buf || len <= 0) return INLA_E_BADARG;
+  buf[0] = 0;
+  if (g_prof.phases.empty()) return 0;
+  cudaEvent_t last;
+  if (cudaEventCreate(&last) != cudaSuccess) return INLA_E_CUDA;
+  cudaEventRecord(last, g_prof.st);
+  cudaEventSynchronize(last);
+  std::vector<std::string> order;
+  std::map<std::string, std::pair<long, double>> acc;
+  for (size_t i = 0; i < g_prof.phases.size(); ++i) {
+    cudaEvent_t next = i + 1 < g_prof.phases.size() ? g_prof.phases[i + 1].first : last;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g_prof.phases[i].first, next);
+    const std::string nm = g_prof.phases[i].second;
+    if (!acc.count(nm)) order.push_back(nm);
+    auto& a = acc[nm];
+    a.first += 1;
+    a.second += ms;
+  }
+  for (auto& p : g_prof.phases) cudaEventDestroy(p.first);
+  cudaEventDestroy(last);
+  g_prof.phases.clear();
+  int off = 0;
+  for (auto& nm : order) {
+    const int w = snprintf(buf + off, len - off, "%s %ld %.4f\n", nm.c_str(), acc[nm].first, acc[nm].second);
+    if (w < 0 || w >= len - off) break;
+    off += w;
+  }
+  return off;
+}
 
 extern "C" void inla_test_profile_enable(int on) { g_prof.on = on != 0; }
 
