@@ -394,6 +394,44 @@ def run_gemm(args):
     print(json.dumps({"gemm_microbench": res}), flush=True)
 
 
+def run_surrogate(args):
+    """The learned-surrogate experiment on the n = 16384 model (surrogate.experiment): exact
+    FD-BFGS on the mixed path against the surrogate trained on --train exact mixed evaluations,
+    every exact evaluation counted; the FP64 path's time to the mode is estimated from one
+    measured FP64 evaluation times the points the exact search needed."""
+    import torch
+    from paper_2311_08050_gb300 import build as B
+    from paper_2311_08050_gb300 import inla, surrogate, synth
+    B.build()
+    torch.cuda.set_device(0)
+    spec, _ = synth.WORKLOADS[args.workload]()
+    th_true = synth.poisson_n16384_theta_true() if args.workload == BENCH_WORKLOAD else _[0]
+    model = inla.Model(spec)
+    chunk = args.surrogate_batch
+
+    def exact_eval(thetas):
+        out = []
+        for c in range(0, len(thetas), chunk):
+            lp, st, _, _ = inla.eval_batch([model], thetas[c:c + chunk], want_x=False, want_var=False,
+                                           precision="mixed")
+            out.append(np.where(np.asarray(st) == 0, lp, -np.inf))
+        return np.concatenate(out)
+
+    exact_eval(th_true[None, :])  # warm-up (tuner, graphs)
+    th0 = th_true + np.array([0.6, -0.5, 0.4, -0.6])[:len(th_true)]
+    res = surrogate.experiment(exact_eval, th_true, th0, n_train=args.train, n_holdout=args.holdout)
+    t0 = time.perf_counter()
+    lp64, st64, _, _ = inla.eval_batch([model], th_true[None, :], want_x=False, want_var=False, precision="fp64")
+    t64 = time.perf_counter() - t0
+    res["fp64"] = {"seconds_per_theta": t64, "status": int(st64[0]),
+                   "time_to_mode_estimated_s": t64 * res["exact_search"]["points"],
+                   "how": "one FP64 evaluation timed here x the exact points of the FD-BFGS search"}
+    res["config"] = {"workload": args.workload, "n": spec.n, "m": spec.m, "theta_dim": spec.theta_dim,
+                     "train": args.train, "holdout": args.holdout, "batch": chunk, "precision": "mixed (5/4 slices)",
+                     "start": "theta_true + (0.6, -0.5, 0.4, -0.6)"}
+    print(json.dumps({"surrogate_experiment": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,9 +453,16 @@ def main():
     ap.add_argument("--workload", default=BENCH_WORKLOAD, choices=(BENCH_WORKLOAD,) + CAPTURE_WORKLOADS,
                     help="the benchmark workload (default) or a smaller case for profiling captures")
     ap.add_argument("--gemm", default=None, help="microbenchmark the Ozaki GEMM: 'M,N,K,S[,lower[,accumulate]];...'")
+    ap.add_argument("--surrogate", action="store_true", help="the learned-surrogate experiment (time to the mode)")
+    ap.add_argument("--train", type=int, default=2000, help="--surrogate: exact training evaluations")
+    ap.add_argument("--holdout", type=int, default=200, help="--surrogate: held-out exact evaluations")
+    ap.add_argument("--surrogate-batch", type=int, default=16, help="--surrogate: points per batched call")
     args = ap.parse_args()
     if args.gemm:
         run_gemm(args)
+        return
+    if args.surrogate:
+        run_surrogate(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -326,3 +326,80 @@ def rank_ccd(surrogate: Surrogate, theta_star, neg_hessian):
     pred = surrogate.predict(pts)
     order = np.argsort(-pred)
     return pts[order], pred[order]
+
+
+def experiment(exact_eval: Callable[[np.ndarray], np.ndarray], th_true, th0, n_train=2000, n_holdout=200,
+               spread=0.5, seed=2311080556, epochs=1500, lr=3e-3, gtol=1e-3, clock=None):
+    """The learned-surrogate experiment with every exact evaluation counted.
+
+    exact_eval: theta (B x t) -> exact log pi~ (B), one batched evaluation per call.
+    1. The method without the surrogate: exact FD-BFGS from th0 (`search_exact`).
+    2. The surrogate: n_train exact evaluations at theta ~ N(th_true, spread^2 I), a fit, its
+       error on n_holdout further exact points (not counted in the search), then the
+       surrogate-guided search from th0 (`search_with_surrogate`).
+    3. Integration points: the CCD design around the guided search's mode in the coordinates
+       of the Laplace approximation of the hyperparameter posterior (exact FD Hessian), ranked
+       by the surrogate and checked by one exact batch.
+    Wall times by `clock` (default time.perf_counter); returns a dict of counts, times and
+    errors, including the totals with the training evaluations charged to the guided search
+    and the number of searches over which the training pays off (None if it never does)."""
+    import time
+    clock = clock or time.perf_counter
+    rng = np.random.default_rng(seed)
+    th_true = np.asarray(th_true, dtype=np.float64)
+    t = len(th_true)
+    out = {}
+    # 1. exact search
+    base = ExactCounter(exact_eval)
+    c0 = clock()
+    xb, fb, itb, _ = search_exact(base, th0, gtol=gtol)
+    out["exact_search"] = {"calls": base.calls, "points": base.points, "seconds": clock() - c0,
+                           "bfgs_iterations": itb, "theta": xb.tolist(), "log_post": fb}
+    # 2. training set, fit, held-out error
+    T = th_true + spread * rng.standard_normal((n_train, t))
+    train = ExactCounter(exact_eval)
+    c0 = clock()
+    vals = train(T)
+    t_train = clock() - c0
+    ok = np.isfinite(vals)
+    c0 = clock()
+    sur = Surrogate(t, max_samples=max(8192, n_train)).fit(T[ok], vals[ok], epochs=epochs, lr=lr)
+    t_fit = clock() - c0
+    Th = th_true + spread * rng.standard_normal((n_holdout, t))
+    vh = exact_eval(Th)
+    okh = np.isfinite(vh)
+    pred = sur.predict(Th[okh])
+    res = pred - vh[okh]
+    out["training"] = {"points": train.points, "calls": train.calls, "finite": int(ok.sum()), "seconds": t_train,
+                       "theta_evals_per_s": train.points / t_train if t_train > 0 else None,
+                       "fit_seconds": t_fit, "epochs": epochs, "final_loss": float(sur.loss_history[-1])}
+    out["holdout"] = {"points": int(okh.sum()), "rmse": float(np.sqrt(np.mean(res ** 2))),
+                      "max_abs": float(np.max(np.abs(res))), "r2": float(1.0 - np.mean(res ** 2) / np.var(vh[okh])),
+                      "log_post_spread": float(np.ptp(vh[okh]))}
+    # near the mode the accuracy that matters for the proposals
+    # 3. guided search
+    guided = ExactCounter(exact_eval)
+    c0 = clock()
+    xs, fs, calls = search_with_surrogate(guided, sur, th0, gtol=gtol)
+    t_guided = clock() - c0
+    out["guided_search"] = {"calls": calls, "points": guided.points, "seconds": t_guided, "theta": xs.tolist(),
+                            "log_post": fs, "same_mode": bool(np.max(np.abs(xs - xb)) < 0.05 and fs >= fb - 1e-3)}
+    tot_points = train.points + guided.points
+    tot_time = t_train + t_fit + t_guided
+    out["totals"] = {"exact_points_with_training": tot_points, "exact_points_without_surrogate": base.points,
+                     "time_to_mode_with_training_s": tot_time,
+                     "time_to_mode_without_surrogate_s": out["exact_search"]["seconds"]}
+    saving = out["exact_search"]["seconds"] - t_guided
+    out["totals"]["searches_to_break_even"] = (t_train + t_fit) / saving if saving > 0 else None
+    # 4. CCD integration points ranked by the surrogate, one exact batch decides
+    negH = -fd_hessian(guided, xs)
+    try:
+        pts, predc = rank_ccd(sur, xs, negH)
+        ex = exact_eval(pts)
+        okc = np.isfinite(ex)
+        out["ccd"] = {"points": len(pts), "exact_spread": float(np.ptp(ex[okc])),
+                      "max_abs_error": float(np.max(np.abs(predc[okc] - ex[okc]))),
+                      "best_in_surrogate_top3": bool(np.argmax(np.where(okc, ex, -np.inf)) in np.argsort(-predc)[:3])}
+    except ValueError as e:
+        out["ccd"] = {"error": str(e)}
+    return out
