@@ -18,7 +18,10 @@ no blocking or fusion of our own):
 * the Laplace approximation log pi~(theta | y) of Eq. (41), written out with all
   normalising constants (see ``evaluate``), and
 * the Gaussian marginals x_i | theta, y ~ N(x_hat_i, (Q*^-1)_ii) (Appendix A.2.1),
-  corrected for the constraints by kriging.
+  corrected for the constraints by kriging, and
+* stage 2: the Hessian of log pi~ at theta*, the CCD / grid exploration points and the
+  latent marginals integrated over them (Section 2, Stage 2; Appendix A.2; readings at the
+  end of this file).
 
 Readings of the paper taken here (the paper is silent or garbled on these):
   Newton tolerance 1e-8 in the infinity norm, at most 50 iterations, step halving
@@ -301,3 +304,88 @@ def evaluate(spec, theta, want_var=True):
     log_post = float(sum(terms.values()))
     return dict(log_post=log_post, x_hat=x_hat, var=var, newton_iters=iters,
                 logdet_Q=logdet_Q, logdet_Qp=logdet_Qp, terms=terms)
+
+
+# ------------------------------------------------------------------------------------
+# Stage 2 (Section 2, Stage 1 and Stage 2; Appendix A.1.2, Eq. (thetatozscale); Appendix A.2):
+# the Hessian of log pi~(theta|y) at theta*, the exploration points of the hyperparameter
+# space, and the latent marginals integrated over them.
+#
+# Readings (the paper cites the grid and CCD strategies without their weights):
+#  * Hessian by central second differences with step h (2 t^2 + 1 evaluations);
+#  * z-coordinates: theta(z) = theta* + V Lambda^-1/2 z, (V, Lambda) the eigenpairs of the
+#    negative Hessian, so z ~ N(0, I) under the Gaussian approximation of pi(theta|y);
+#  * CCD: the centre plus the factorial points (+-1)^t (a half fraction with
+#    x_t = x_1 ... x_{t-1} for t >= 5, giving the 45 points of t = 6) and the 2t axial points,
+#    every non-centre point on the sphere of radius f0 sqrt(t); quadrature weight 1 at the
+#    centre and delta = exp(f0^2 t / 2) / (N (f0^2 - 1)) at the N others, the value for which a
+#    Gaussian pi(theta|y) has its variance reproduced exactly;
+#  * grid: the points dz * k, |k_i| dz <= z_max, equal weights;
+#  * integration weights w_k ~ delta_k pi~(theta_k|y) (the linear map's Jacobian is constant),
+#    and the integrated marginal of x_i is the mixture of the Gaussian marginals
+#    N(x_hat_i(theta_k), var_i(theta_k)): mean sum_k w_k x_hat_i, variance
+#    sum_k w_k (var_i + x_hat_i^2) - mean^2.
+# ------------------------------------------------------------------------------------
+
+def hessian_fd(f, theta, h):
+    """Central second differences of a scalar function f at theta (t x t):
+    (f(+h e_i) - 2 f(0) + f(-h e_i)) / h^2 on the diagonal and
+    (f(+,+) - f(+,-) - f(-,+) + f(-,-)) / (4 h^2) off it."""
+    theta = np.asarray(theta, dtype=np.float64)
+    t = theta.size
+    E = np.eye(t) * h
+    f0 = f(theta)
+    H = np.zeros((t, t))
+    for i in range(t):
+        H[i, i] = (f(theta + E[i]) - 2.0 * f0 + f(theta - E[i])) / (h * h)
+        for j in range(i + 1, t):
+            H[i, j] = H[j, i] = (f(theta + E[i] + E[j]) - f(theta + E[i] - E[j]) - f(theta - E[i] + E[j])
+                                 + f(theta - E[i] - E[j])) / (4.0 * h * h)
+    return H
+
+
+def ccd_design(t, f0=1.1):
+    """CCD points in z-coordinates and their quadrature weights (see the readings above)."""
+    import itertools
+    corners = [np.array(c, dtype=np.float64) for c in itertools.product((-1.0, 1.0), repeat=t)]
+    if t >= 5:
+        corners = [c for c in corners if c[-1] == np.prod(c[:-1])]
+    axial = [s * np.eye(t)[i] for i in range(t) for s in (1.0, -1.0)]
+    dirs = corners + axial
+    pts = [np.zeros(t)] + [d / np.linalg.norm(d) * f0 * math.sqrt(t) for d in dirs]
+    N = len(dirs)
+    delta = math.exp(f0 * f0 * t / 2.0) / (N * (f0 * f0 - 1.0))
+    return np.array(pts), np.array([1.0] + [delta] * N)
+
+
+def grid_design(t, dz, z_max):
+    """Grid points dz * k with |k_i| dz <= z_max, equal weights."""
+    import itertools
+    K = int(math.floor(z_max / dz + 1e-12))
+    ks = np.arange(-K, K + 1) * dz
+    pts = np.array(list(itertools.product(ks, repeat=t)), dtype=np.float64)
+    return pts, np.ones(len(pts))
+
+
+def z_to_theta(theta_star, neg_hessian, Z):
+    """theta(z) = theta* + V Lambda^-1/2 z for each row z of Z."""
+    lam, V = np.linalg.eigh(np.asarray(neg_hessian, dtype=np.float64))
+    if np.min(lam) <= 0:
+        raise ValueError("the negative Hessian is not positive definite")
+    return np.asarray(theta_star, dtype=np.float64)[None, :] + (np.atleast_2d(Z) / np.sqrt(lam)[None, :]) @ V.T
+
+
+def integrate_marginals(spec, theta_star, neg_hessian, Z, delta):
+    """Integrated Gaussian marginals of the latent field over the exploration points:
+    evaluate every theta_k, weight w_k ~ delta_k exp(log pi~(theta_k|y)), and return the
+    mixture's mean and variance per latent element."""
+    thetas = z_to_theta(theta_star, neg_hessian, Z)
+    res = [evaluate(spec, th) for th in thetas]
+    lp = np.array([r["log_post"] for r in res])
+    w = np.asarray(delta, dtype=np.float64) * np.exp(lp - lp.max())
+    w = w / w.sum()
+    X = np.array([r["x_hat"] for r in res])
+    Vv = np.array([r["var"] for r in res])
+    mean = w @ X
+    var = w @ (Vv + X * X) - mean * mean
+    return dict(mean=mean, var=var, weights=w, thetas=thetas, log_post=lp)

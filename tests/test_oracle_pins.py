@@ -448,3 +448,91 @@ def test_log_post_invariant_to_latent_permutation():
     assert abs(r["log_post"] - r2["log_post"]) < 1e-9 * abs(r["log_post"])
     assert np.max(np.abs(r["x_hat"][1:][perm] - r2["x_hat"][1:])) < 1e-9
     assert np.max(np.abs(r["var"][1:][perm] / r2["var"][1:] - 1)) < 1e-9
+
+
+# ---------------------------------------------------------------------------------
+# stage 2: Hessian, exploration points, integrated latent marginals
+# ---------------------------------------------------------------------------------
+
+def test_ccd_design_counts_and_gaussian_moments():
+    """45 CCD points for t = 6 (the number the paper's hyperparameter exploration cites, with
+    the half fraction of the factorial part); for every t, an exactly Gaussian pi(theta|y)
+    (log density -|z|^2 / 2) weighted by the design's quadrature weights has mean 0 and
+    covariance I, the moments of N(0, I)."""
+    assert len(O.ccd_design(6)[0]) == 45
+    assert [len(O.ccd_design(t)[0]) for t in (2, 3, 4, 5)] == [9, 15, 25, 27]
+    for t in (2, 3, 4, 5, 6):
+        Z, d = O.ccd_design(t)
+        w = d * np.exp(-0.5 * np.sum(Z * Z, axis=1))
+        w /= w.sum()
+        assert np.max(np.abs(w @ Z)) < 1e-12
+        assert np.max(np.abs((Z * w[:, None]).T @ Z - np.eye(t))) < 1e-12
+
+
+def test_hessian_fd_exact_on_quadratics_and_second_order_on_cubics():
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((3, 3))
+    M = M + M.T
+    b = rng.standard_normal(3)
+    x0 = rng.standard_normal(3)
+    H = O.hessian_fd(lambda x: 0.5 * x @ M @ x + b @ x + 3.0, x0, 0.1)
+    assert np.max(np.abs(H - M)) < 1e-12
+    # cubic term c (x . u)^3: exact Hessian 6 c (x . u) u u^T; central differences carry
+    # an O(h^2) error on the off-diagonal only in the mixed fourth-order terms (here zero)
+    u = np.array([0.3, -0.2, 0.5])
+    f = lambda x: (x @ u) ** 3
+    H = O.hessian_fd(f, x0, 1e-3)
+    assert np.max(np.abs(H - 6.0 * (x0 @ u) * np.outer(u, u))) < 1e-7
+
+
+def _iid_gauss_model(seed, n=6, m=15, tau_y=4.0):
+    """Gaussian likelihood on one iid block of precision exp(theta): t = 1, every posterior
+    quantity in closed form."""
+    rng = np.random.default_rng(seed)
+    cols = [np.array(sorted(rng.choice(n, 2, replace=False))) for _ in range(m)]
+    vals = [rng.uniform(0.5, 1.5, 2) for _ in range(m)]
+    A = CSR.from_rows(m, n, cols, vals)
+    y = rng.standard_normal(m) * 1.5
+    off = 0.2 * rng.standard_normal(m)
+    # a Gaussian prior on the log precision keeps the posterior's tails light (with a PC prior
+    # the right tail follows the prior's exp(-theta / 2) and no finite range holds the integral)
+    return ModelSpec("iid_gauss", n, "gaussian", A, y, off, [Block("iid", n, theta_idx=0)],
+                     [("gauss", 1.0, 0.7)], lik_prec=tau_y)
+
+
+def test_grid_integration_matches_adaptive_quadrature_of_the_closed_forms():
+    """For a Gaussian likelihood pi~(theta|y) and pi(x|theta, y) are exact, so the integrated
+    marginals are the exact posterior moments of x_i.  The oracle's grid integration (dz = 0.2
+    in the z-coordinates of the Laplace approximation, |z| <= 9) against adaptive quadrature
+    over theta of the closed forms: pi(theta|y) from N(y; o, e^-theta A A^T + I / tau_y) and the
+    Gaussian conditional moments of x."""
+    spec = _iid_gauss_model(1)
+    A = spec.A.to_dense()
+    tau_y = spec.lik_prec
+
+    def closed(theta):
+        S = math.exp(-theta) * np.eye(spec.n)
+        cov_y = A @ S @ A.T + np.eye(spec.m) / tau_y
+        lp = O.log_theta_prior(spec, [theta]) + multivariate_normal(spec.offset, cov_y).logpdf(spec.y)
+        K = S @ A.T @ np.linalg.inv(cov_y)
+        mu = K @ (spec.y - spec.offset)
+        var = np.diag(S - K @ A @ S)
+        return lp, mu, var
+
+    res = so.minimize_scalar(lambda th: -closed(th)[0], bounds=(-5, 8), method="bounded",
+                             options=dict(xatol=1e-10))
+    th_star = res.x
+    negH = -O.hessian_fd(lambda th: O.evaluate(spec, th)["log_post"], np.array([th_star]), 1e-3)
+    sd = 1.0 / math.sqrt(negH[0, 0])
+    lp_star = closed(th_star)[0]
+    lo, hi = th_star - 14 * sd, th_star + 14 * sd
+    Zc = quad(lambda th: math.exp(closed(th)[0] - lp_star), lo, hi, epsabs=0, epsrel=1e-12, limit=200)[0]
+    mean = np.array([quad(lambda th: closed(th)[1][i] * math.exp(closed(th)[0] - lp_star), lo, hi,
+                          epsabs=0, epsrel=1e-12, limit=200)[0] for i in range(spec.n)]) / Zc
+    second = np.array([quad(lambda th: (closed(th)[2][i] + closed(th)[1][i] ** 2) * math.exp(closed(th)[0] - lp_star),
+                            lo, hi, epsabs=0, epsrel=1e-12, limit=200)[0] for i in range(spec.n)]) / Zc
+    var = second - mean ** 2
+    Z, d = O.grid_design(1, 0.2, 9.0)
+    r = O.integrate_marginals(spec, np.array([th_star]), negH, Z, d)
+    assert np.max(np.abs(r["mean"] - mean)) <= 1e-7 * np.max(np.abs(mean))
+    assert np.max(np.abs(r["var"] / var - 1.0)) <= 1e-7
