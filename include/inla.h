@@ -169,6 +169,22 @@ int inla_eval_batch(inla_model *const *models, int32_t nmodels, const int32_t *m
 int inla_marginals(inla_model *model, const double *theta, const inla_opts *opts,
                    double *mean, double *var);
 
+/* Stage 2 (Section 2, Stage 2; Appendix A.2): the latent marginals integrated over K
+ * exploration points theta_k of the hyperparameter space (a CCD or grid design).  Inputs per
+ * point: log_post[k] = log pi~(theta_k|y) and the Gaussian marginals of that point, rows k of
+ * x_hat and var (K x ld, row-major; n <= ld used per row), e.g. from inla_eval_batch;
+ * delta[k] >= 0: the design's quadrature weight.  With w_k proportional to
+ * delta_k exp(log_post[k]) (normalised; points with a non-finite log_post weigh 0), writes
+ * the mixture's moments mean_i = sum_k w_k x_hat_ki and var_i = sum_k w_k (var_ki + x_hat_ki^2)
+ * - mean_i^2 (n doubles each).  log_post and delta are host arrays; x_hat, var, mean and
+ * var_out are device pointers on the current device with INLA_OPT_DEVICE_OUT in flags, host
+ * arrays otherwise.  K <= 4096.  stream: cudaStream_t or NULL; the call synchronizes it.
+ * Errors: INLA_E_BADARG (sizes, negative or non-finite delta, no point with weight),
+ * INLA_E_NOMEM, INLA_E_CUDA. */
+int inla_integrate_marginals(int32_t K, int32_t n, const double *log_post, const double *delta,
+                             const double *x_hat, const double *var, int64_t ld, double *mean,
+                             double *var_out, int32_t flags, void *stream);
+
 /* Static text for a status code. */
 const char *inla_status_string(int status);
 
