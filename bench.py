@@ -226,18 +226,25 @@ def run_ours(args):
     L.inla_test_profile_enable(0)
     stats = (C.c_double * 5)()
     L.inla_test_stats_read(stats)
-    pbuf = C.create_string_buffer(1 << 16)
-    L.inla_test_profile_read(pbuf, 1 << 16)
+    pbuf = C.create_string_buffer(1 << 18)
+    L.inla_test_profile_read_by_phase(pbuf, 1 << 18)
     phbuf = C.create_string_buffer(1 << 12)
     L.inla_test_phase_read(phbuf, 1 << 12)
     phases = []
     for line in phbuf.value.decode().splitlines():
         name, cnt, tot = line.split()
         phases.append({"phase": name, "ms": round(float(tot), 3)})
-    breakdown = []
+    by_kernel, by_phase = {}, {}
     for line in pbuf.value.decode().splitlines():
-        name, cnt, tot = line.split()
-        breakdown.append({"kernel": name, "launches": int(cnt), "ms": round(float(tot), 3)})
+        key, cnt, tot = line.split()
+        phase, name = key.split("/", 1)
+        k = by_kernel.setdefault(name, [0, 0.0])
+        k[0] += int(cnt)
+        k[1] += float(tot)
+        by_phase.setdefault(phase, []).append({"kernel": name, "launches": int(cnt), "ms": round(float(tot), 3)})
+    breakdown = sorted(({"kernel": k, "launches": v[0], "ms": round(v[1], 3)} for k, v in by_kernel.items()),
+                       key=lambda b: -b["ms"])
+    phase_kernels = {ph: sorted(v, key=lambda b: -b["ms"])[:6] for ph, v in by_phase.items()}
     step_ms_prof = sum(b["ms"] for b in breakdown) or 1.0
     for b in breakdown:
         b["share"] = round(b["ms"] / step_ms_prof, 4)
@@ -291,7 +298,7 @@ def run_ours(args):
                       "outer_block_tuned": outer_block,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
            "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
-           "kernel_breakdown": breakdown[:12], "phase_breakdown": phases}
+           "kernel_breakdown": breakdown[:12], "phase_breakdown": phases, "phase_kernels": phase_kernels}
     # ---------------- end to end from host buffers ----------------
     if not args.no_e2e:
         from paper_2311_08050_gb300.synth import ModelSpec  # noqa: F401

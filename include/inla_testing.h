@@ -57,6 +57,8 @@ int inla_test_profile_read(char *buf, int len);
  * Newton of the points that start from another point's mode, their factor, and the
  * log-determinants, variances and log pi~); resets and returns the bytes written. */
 int inla_test_phase_read(char *buf, int len);
+/* As inla_test_profile_read, the lines keyed "phase/kernel" (the phase in force at the launch). */
+int inla_test_profile_read_by_phase(char *buf, int len);
 
 /* Dense covariance entries sigma2 * exp(-sqrt((dx * inv_rx)^2 + (dy * inv_ry)^2)) for n <= 8192
  * host points (row-major n x 2), computed by the mixed path's double-float device code (its own

@@ -208,7 +208,7 @@ static int op_prior_dense(Batch& B) {
 static int op_variances(Batch& B) {
   if (B.mixed) {
     INLA_TRY(mixed_inverse_factor(B, SEL_L, true));
-    launch_colsumsq_wk_df(B.d_slots, B.n, B.max_t, B.st);
+    launch_rowsumsq_wk_df(B.d_slots, B.n, B.max_n, B.st);
     if (B.max_k > 0) {
       INLA_TRY(mixed_var_constraint(B));
       launch_var_finish(B.d_slots, B.n, B.max_n, B.st);

@@ -314,23 +314,65 @@ static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, i
   return INLA_OK;
 }
 
-// W = F^-1 (lower), written into Wk (into_wk) or into L
+// Y = F^-T (upper triangular: the transpose of the inverse of the lower factor F), written into
+// Wk (into_wk) or into L.  Column blocks of Y in increasing order: Y[:, K] = Y[:, K] Linv_K^T, then
+// Y[:, J] -= Y[:, K] F[J, K]^T for the blocks J > K -- the transpose of forward substitution on
+// the rows of F^-1, so that every operand is sliced by rows (Y's column block and F's row block
+// are both K-contiguous) and only the first kend rows of Y (its nonzero part) enter.
 int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
   const MRef F = mref(B, sel);
   const Slot& s0 = B.h[0];
-  float2* W = reinterpret_cast<float2*>(into_wk ? s0.Wk : s0.L);
+  const int n = F.n, S = B.S;
+  float2* Y = reinterpret_cast<float2*>(into_wk ? s0.Wk : s0.L);
+  const int64_t ys = B.mat_stride;
+  const int ld = B.np;
   for (int i = 0; i < B.n; ++i)
     cudaMemsetAsync(into_wk ? B.h[i].Wk : B.h[i].L, 0, (size_t)B.mat_stride * 8, B.st);
-  launch_diag_ones_df(W, B.mat_stride, B.np, F.n, B.n, B.st);
-  return trsm_left(B, sel, W, B.mat_stride, B.np, F.n, true);
+  launch_diag_ones_df(Y, ys, ld, n, B.n, B.st);
+  for (int K0 = 0; K0 < n; K0 += NB) {
+    const int kend = std::min(K0 + NB, n);
+    const int nc = kend;  // rows of Y that can be nonzero in columns [K0, kend)
+    for (int j0 = K0; j0 < kend; j0 += IB) {
+      // Y[0:nc, j0 tile] = Y[0:nc, j0 tile] Linv_j^T
+      OzOperand py = operand(B.PA, B.EA, nc, IB);
+      OzOperand pl = operand(B.PB, B.EB, IB, IB);
+      oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py, S, B.n, B.st);
+      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB,
+                  false, pl, S, B.n, B.st);
+      OzArgs a = gemm_args(B, Y + j0, ys, ld, nc, IB, IB, 0.f, 1.f);
+      INLA_TRY(oz_gemm(py, pl, a, B.n, B.st));
+      if (j0 + IB < kend) {
+        // Y[0:nc, j0+64 .. kend] -= Y[0:nc, j0 tile] F[j0+64 .. kend, j0 tile]^T
+        const int R = kend - j0 - IB;
+        OzOperand py2 = operand(B.PA, B.EA, nc, IB);
+        OzOperand pf = operand(B.PB, B.EB, R, IB);
+        oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py2, S, B.n, B.st);
+        oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, B.st);
+        OzArgs u = gemm_args(B, Y + j0 + IB, ys, ld, nc, R, IB, 1.f, -1.f);
+        INLA_TRY(oz_gemm(py2, pf, u, B.n, B.st));
+      }
+    }
+    const int R = n - kend;
+    if (R > 0) {
+      // Y[0:nc, kend .. n] -= Y[0:nc, K0:kend] F[kend .. n, K0:kend]^T
+      OzOperand py = operand(B.PA, B.EA, nc, kend - K0);
+      OzOperand pf = operand(B.PB, B.EB, R, kend - K0);
+      oz_slice_df(Y, ys, ld, 0, K0, nc, kend - K0, false, py, S, B.n, B.st);
+      oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, B.st);
+      OzArgs u = gemm_args(B, Y + kend, ys, ld, nc, R, kend - K0, 1.f, -1.f);
+      INLA_TRY(oz_gemm(py, pf, u, B.n, B.st));
+    }
+  }
+  return INLA_OK;
 }
 
-// Q_p[0:nd, 0:nd] = W^T W with W = L_Sigma^-1 held in L (lower)
+// Q_p[0:nd, 0:nd] = W^T W = Y Y^T with Y = L_Sigma^-T held in L (upper): row k of Y is nonzero
+// from column k on, so the lower tiles (m0 >= n0) need k >= m0 only
 int mixed_lauum_cov(Batch& B) {
   const Slot& s0 = B.h[0];
   const int ndp = B.ndp, nd = s0.nd, S = B.S;
   OzOperand pw = operand(B.PBIG, B.EBIG, ndp, ndp);
-  oz_slice_df(reinterpret_cast<float2*>(s0.L), B.mat_stride, B.np, 0, 0, ndp, ndp, true, pw, S, B.n, B.st);
+  oz_slice_df(reinterpret_cast<float2*>(s0.L), B.mat_stride, B.np, 0, 0, ndp, ndp, false, pw, S, B.n, B.st);
   float2* C = reinterpret_cast<float2*>(s0.Qp) + (int64_t)s0.nd_off * B.np + s0.nd_off;
   OzArgs a = gemm_args(B, C, B.mat_stride, B.np, nd, nd, ndp, 0.f, 1.f);
   a.lower = 1;
@@ -355,7 +397,8 @@ int mixed_schur(Batch& B) {
   return mixed_potrf(B, SEL_S);
 }
 
-// t2 = colsumsq(L_S^-1 Z^T W), W = Q*^-1 factor inverse in Wk; uses L as scratch
+// t2 = colsumsq(L_S^-1 Z^T W), W = Q*^-1's factor inverse, held transposed (Y = W^T) in Wk; uses
+// L as scratch.  G = Z^T W = Z^T Y^T: B operand = the rows of Y
 int mixed_var_constraint(Batch& B) {
   const Slot& s0 = B.h[0];
   const int S = B.S;
@@ -365,7 +408,7 @@ int mixed_var_constraint(Batch& B) {
   OzOperand pz = operand(B.PA, B.EA, B.kp, B.np);
   oz_slice_df(Z, B.z_stride, B.kp, 0, 0, B.kp, B.np, true, pz, S, B.n, B.st);
   OzOperand pw = operand(B.PBIG, B.EBIG, B.np, B.np);
-  oz_slice_df(W, B.mat_stride, B.np, 0, 0, B.np, B.np, true, pw, S, B.n, B.st);
+  oz_slice_df(W, B.mat_stride, B.np, 0, 0, B.np, B.np, false, pw, S, B.n, B.st);
   OzArgs a = gemm_args(B, G, B.mat_stride, B.np, B.kp, B.np, B.np, 0.f, 1.f);
   a.k_mode = 2;
   INLA_TRY(oz_gemm(pz, pw, a, B.n, B.st));

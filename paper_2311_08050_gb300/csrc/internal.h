@@ -13,6 +13,8 @@ constexpr int TB = 64;        // FP64 tile edge
 constexpr int PAD = 256;      // latent and dense-block padding unit
 constexpr int MAX_THETA = 16;
 constexpr int MAX_KRON = 8;
+constexpr int HEAVY_LEN = 4096;     // contributions above which a block, not a warp, reduces a sum
+constexpr int HEAVY_BLOCKS = 8;     // blocks of a launch given to the heavy sums
 
 #define INLA_CUDA_TRY(expr)                                  \
   do {                                                       \
@@ -77,6 +79,11 @@ struct ModelDev {
   int64_t *At_rowptr; int32_t *At_row; double *At_val;     // n_pad x m (transpose)
   int64_t npairs;
   int32_t *pair_row, *pair_col; int64_t *pair_ptr;         // unique (row >= col) pairs
+  // rows of A^T and pairs with more than HEAVY_LEN contributions (e.g. an intercept that every
+  // observation loads): reduced by whole blocks instead of one warp each
+  int32_t n_heavy_cols, n_heavy_pairs;
+  int32_t* heavy_cols;
+  int64_t* heavy_pairs;
   int32_t *pc_obs; double *pc_coef;                        // contributions
   double *y, *offset;                                      // offset may be null
   double lgamma_sum;                                       // sum log y! (Poisson)

@@ -116,11 +116,26 @@ __global__ void __launch_bounds__(256) k_add_pairs_df(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
   const ModelDev& md = *s.md;
+  if (blockIdx.x < HEAVY_BLOCKS) {  // heavy pairs: a whole block each (fixed-order tree)
+    for (int h = blockIdx.x; h < md.n_heavy_pairs; h += HEAVY_BLOCKS) {
+      const int64_t p = md.heavy_pairs[h];
+      double v = 0.0;
+      for (int64_t c = md.pair_ptr[p] + threadIdx.x; c < md.pair_ptr[p + 1]; c += 256)
+        v = fma(s.w[md.pc_obs[c]], md.pc_coef[c], v);
+      v = block_sum_256(v);
+      if (threadIdx.x == 0) {
+        float2* q = dfm(s.L) + (size_t)md.pair_row[p] * s.n_pad + md.pair_col[p];
+        df_store(q, df_add(df_load(q), df_from_double(v)));
+      }
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp0 = ((blockIdx.x - HEAVY_BLOCKS) * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)(gridDim.x - HEAVY_BLOCKS) * blockDim.x) >> 5;
   for (int64_t p = warp0; p < md.npairs; p += nwarps) {
     const int64_t lo = md.pair_ptr[p], hi = md.pair_ptr[p + 1];
+    if (hi - lo > HEAVY_LEN) continue;
     double v = 0.0;
     for (int64_t c = lo + lane; c < hi; c += 32) v = fma(s.w[md.pc_obs[c]], md.pc_coef[c], v);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -542,6 +557,25 @@ __global__ void __launch_bounds__(256) k_colsumsq_wk_df(Slot* slots) {
   if (threadIdx.x < TB)
     s.t1[jt * TB + threadIdx.x] = ((part[0][threadIdx.x] + part[1][threadIdx.x]) + part[2][threadIdx.x]) + part[3][threadIdx.x];
 }
+// t1[j] = sum_{k >= j} Wk[j][k]^2 (df64 Y = W^T, upper): the column sums of squares of W read
+// along rows of Y, one warp per row (coalesced)
+__global__ void __launch_bounds__(256) k_rowsumsq_wk_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const int lane = threadIdx.x & 31;
+  const float2* Y = dfm(s.Wk);
+  for (int j = (blockIdx.x * 256 + threadIdx.x) >> 5; j < s.n_pad; j += (gridDim.x * 256) >> 5) {
+    df acc = df_make(0.f, 0.f);
+    const float2* row = Y + (size_t)j * s.n_pad;
+    for (int k = j + lane; k < s.n_pad; k += 32) {
+      const df w = df_load(row + k);
+      acc = df_fma(acc, w, w);
+    }
+    double r = df_to_double(acc);
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) s.t1[j] = r;
+  }
+}
 // t2[j] = sum_{r < k_pad} L[r][j]^2 (df64 k_pad x n_pad held in L)
 __global__ void __launch_bounds__(256) k_colsumsq_gt_df(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
@@ -575,7 +609,7 @@ void launch_prior_entries_df(Slot* slots, int nslots, int64_t max_entries, cudaS
 }
 void launch_add_pairs_df(Slot* slots, int nslots, int64_t max_pairs, cudaStream_t st) {
   if (max_pairs > 0)
-    count_launch("k_add_pairs_df"), k_add_pairs_df<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
+    count_launch("k_add_pairs_df"), k_add_pairs_df<<<dim3(HEAVY_BLOCKS + (unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_qp_gemv_df(Slot* slots, int nslots, int which, int max_n, cudaStream_t st) {
   count_launch("k_vec_to_df"), k_vec_to_df<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
@@ -623,6 +657,9 @@ void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_
 }
 void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st) {
   count_launch("k_colsumsq_wk_df"), k_colsumsq_wk_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);
+}
+void launch_rowsumsq_wk_df(Slot* slots, int nslots, int max_n, cudaStream_t st) {
+  count_launch("k_rowsumsq_wk_df"), k_rowsumsq_wk_df<<<dim3(std::min(2048, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st) {
   count_launch("k_colsumsq_gt_df"), k_colsumsq_gt_df<<<dim3(max_t, nslots), 256, 0, st>>>(slots);

@@ -117,11 +117,23 @@ __global__ void __launch_bounds__(256) k_add_pairs(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
   const ModelDev& md = *s.md;
+  if (blockIdx.x < HEAVY_BLOCKS) {  // heavy pairs: a whole block each
+    for (int h = blockIdx.x; h < md.n_heavy_pairs; h += HEAVY_BLOCKS) {
+      const int64_t p = md.heavy_pairs[h];
+      double v = 0.0;
+      for (int64_t c = md.pair_ptr[p] + threadIdx.x; c < md.pair_ptr[p + 1]; c += 256)
+        v = fma(s.w[md.pc_obs[c]], md.pc_coef[c], v);
+      v = block_sum_256(v);
+      if (threadIdx.x == 0) s.L[(size_t)md.pair_row[p] * s.n_pad + md.pair_col[p]] += v;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp0 = ((blockIdx.x - HEAVY_BLOCKS) * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)(gridDim.x - HEAVY_BLOCKS) * blockDim.x) >> 5;
   for (int64_t p = warp0; p < md.npairs; p += nwarps) {
     const int64_t lo = md.pair_ptr[p], hi = md.pair_ptr[p + 1];
+    if (hi - lo > HEAVY_LEN) continue;
     double v = 0.0;
     for (int64_t c = lo + lane; c < hi; c += 32) v = fma(s.w[md.pc_obs[c]], md.pc_coef[c], v);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -247,12 +259,27 @@ __global__ void __launch_bounds__(256) k_quad(Slot* slots, int which) {
 
 // g = A^T r - t1, one warp per latent entry (a column of A such as an intercept can carry
 // every observation); lanes stride the column, fixed-order shuffle reduction
+// The first HEAVY_BLOCKS blocks reduce the heavy rows of A^T (a whole block each, fixed-order
+// tree); the others take one warp per remaining row.
 __global__ void __launch_bounds__(256) k_gradient(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
   const ModelDev& md = *s.md;
+  if (blockIdx.x < HEAVY_BLOCKS) {
+    for (int h = blockIdx.x; h < md.n_heavy_cols; h += HEAVY_BLOCKS) {
+      const int j = md.heavy_cols[h];
+      double a = 0.0;
+      for (int64_t e = md.At_rowptr[j] + threadIdx.x; e < md.At_rowptr[j + 1]; e += 256)
+        a = fma(md.At_val[e], s.eta[md.At_row[e]], a);
+      a = block_sum_256(a);
+      if (threadIdx.x == 0) s.g[j] = a - s.t1[j];
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
-  for (int j = (blockIdx.x * 256 + threadIdx.x) >> 5; j < s.n_pad; j += (gridDim.x * 256) >> 5) {
+  const int nb = gridDim.x - HEAVY_BLOCKS;
+  for (int j = ((blockIdx.x - HEAVY_BLOCKS) * 256 + threadIdx.x) >> 5; j < s.n_pad; j += (nb * 256) >> 5) {
+    if (md.At_rowptr[j + 1] - md.At_rowptr[j] > HEAVY_LEN) continue;
     double a = 0.0;
     for (int64_t e = md.At_rowptr[j] + lane; e < md.At_rowptr[j + 1]; e += 32) a = fma(md.At_val[e], s.eta[md.At_row[e]], a);
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -407,7 +434,8 @@ void launch_copy_qp_to_l(Slot* slots, int nslots, int max_t, cudaStream_t st) {
   count_launch("k_copy_qp_to_l"), k_copy_qp_to_l<<<dim3(tri(max_t), nslots), 256, 0, st>>>(slots);
 }
 void launch_add_pairs(Slot* slots, int nslots, int64_t max_pairs, cudaStream_t st) {
-  if (max_pairs > 0) count_launch("k_add_pairs"), k_add_pairs<<<dim3((unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
+  if (max_pairs > 0)
+    count_launch("k_add_pairs"), k_add_pairs<<<dim3(HEAVY_BLOCKS + (unsigned)std::min<int64_t>(4096, (max_pairs + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_prior_logdet(Slot* slots, int nslots, cudaStream_t st) { count_launch("k_prior_logdet"), k_prior_logdet<<<nslots, 256, 0, st>>>(slots); }
 void launch_theta_prior(Slot* slots, int nslots, cudaStream_t st) { count_launch("k_theta_prior"), k_theta_prior<<<nslots, 32, 0, st>>>(slots); }
@@ -422,7 +450,7 @@ void launch_qp_gemv(Slot* slots, int nslots, int which, int max_n, cudaStream_t 
 }
 void launch_quad(Slot* slots, int nslots, int which, cudaStream_t st) { count_launch("k_quad"), k_quad<<<nslots, 256, 0, st>>>(slots, which); }
 void launch_gradient(Slot* slots, int nslots, int max_n, cudaStream_t st) {
-  count_launch("k_gradient"), k_gradient<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
+  count_launch("k_gradient"), k_gradient<<<dim3(HEAVY_BLOCKS + std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
 }
 void launch_wls_start(Slot* slots, int nslots, int max_m, int max_n, cudaStream_t st) {
   count_launch("k_wls_start"), k_wls_start<<<dim3(vgrid(std::max(max_m, max_n)), nslots), 256, 0, st>>>(slots);

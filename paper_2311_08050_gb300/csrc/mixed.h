@@ -30,6 +30,7 @@ struct TrsvArgs {
 int launch_trsv_df(const TrsvArgs& a, cudaStream_t st);
 void launch_logdet_df(Slot* slots, int nslots, int sel, int out_idx, cudaStream_t st);
 void launch_colsumsq_wk_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
+void launch_rowsumsq_wk_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
 void launch_colsumsq_gt_df(Slot* slots, int nslots, int max_t, cudaStream_t st);
 void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int nslots, cudaStream_t st);
 
@@ -71,8 +72,8 @@ struct Batch {
 int mixed_potrf(Batch& B, int sel);          // replays a captured CUDA graph for a known layout
 void mixed_graphs_clear();                   // drop every captured graph (workspace reallocated)
 int mixed_nb_choice(int n, int S);           // the tuned outer block for (n, S), 0 if undecided
-int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // W = F^-1 (lower), F by sel
-int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = W^T W (W in L)
+int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // Y = F^-T (upper), F by sel
+int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = Y Y^T (Y in L)
 int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S
 int mixed_var_constraint(Batch& B);                           // t2 = diag(Q^-1 C^T S^-1 C Q^-1)
 

@@ -281,6 +281,14 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   }
   pptr.push_back((int64_t)con.size());
   d.npairs = (int64_t)prow.size();
+  std::vector<int32_t> heavy_cols;
+  for (int j = 0; j < n_pad; ++j)
+    if (Atp[j + 1] - Atp[j] > HEAVY_LEN) heavy_cols.push_back(j);
+  std::vector<int64_t> heavy_pairs;
+  for (int64_t q = 0; q < d.npairs; ++q)
+    if (pptr[q + 1] - pptr[q] > HEAVY_LEN) heavy_pairs.push_back(q);
+  d.n_heavy_cols = (int32_t)heavy_cols.size();
+  d.n_heavy_pairs = (int32_t)heavy_pairs.size();
   if (D->likelihood == INLA_LIK_POISSON) {
     double s = 0.0;
     for (int i = 0; i < m; ++i) s += std::lgamma(D->y[i] + 1.0);
@@ -443,6 +451,8 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   INLA_TRY(dev_copy(M, &d.pair_ptr, pptr.data(), pptr.size()));
   INLA_TRY(dev_copy(M, &d.pc_obs, pobs.data(), pobs.size()));
   INLA_TRY(dev_copy(M, &d.pc_coef, pcoef.data(), pcoef.size()));
+  INLA_TRY(dev_copy(M, &d.heavy_cols, heavy_cols.data(), heavy_cols.size()));
+  INLA_TRY(dev_copy(M, &d.heavy_pairs, heavy_pairs.data(), heavy_pairs.size()));
   INLA_TRY(dev_copy(M, &d.y, D->y, (size_t)m));
   if (D->offset) INLA_TRY(dev_copy(M, &d.offset, D->offset, (size_t)m));
   INLA_TRY(dev_copy(M, &d.entries, ent.data(), ent.size()));

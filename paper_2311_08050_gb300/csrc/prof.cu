@@ -13,10 +13,16 @@
 namespace inla {
 
 namespace {
+struct ProfEvent {
+  cudaEvent_t ev;
+  const char* kernel;
+  const char* phase;  // the phase mark in force when the kernel was launched ("" before any)
+};
 struct Prof {
   bool on = false;
   cudaStream_t st = nullptr;
-  std::vector<std::pair<cudaEvent_t, const char*>> ev;
+  const char* phase = "";
+  std::vector<ProfEvent> ev;
   std::vector<std::pair<cudaEvent_t, const char*>> phases;  // phase boundaries of a batch
 };
 Prof g_prof;
@@ -31,7 +37,7 @@ int count_launch(const char* name) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) == cudaSuccess) {
       cudaEventRecord(e, g_prof.st);
-      g_prof.ev.push_back({e, name});
+      g_prof.ev.push_back({e, name, g_prof.phase});
     }
   }
   return 0;
@@ -39,6 +45,7 @@ int count_launch(const char* name) {
 
 void prof_phase(const char* name) {
   if (!g_prof.on) return;
+  g_prof.phase = name;
   cudaEvent_t e;
   if (cudaEventCreate(&e) == cudaSuccess) {
     cudaEventRecord(e, g_prof.st);
@@ -84,11 +91,16 @@ extern "C" int inla_test_phase_read(char* buf, int len) {
   return off;
 }
 
-extern "C" void inla_test_profile_enable(int on) { g_prof.on = on != 0; }
+
+extern "C" void inla_test_profile_enable(int on) {
+  g_prof.on = on != 0;
+  g_prof.phase = "";
+}
 
 // Writes "name launches total_ms\n" lines (largest total first) into buf; returns the
 // number of bytes written (0 if nothing was recorded), or a negative status.
-extern "C" int inla_test_profile_read(char* buf, int len) {
+// by_phase: key "phase/kernel" instead of "kernel"
+static int profile_read(char* buf, int len, bool by_phase) {
   if (!buf || len <= 0) return INLA_E_BADARG;
   buf[0] = 0;
   if (g_prof.ev.empty()) return 0;
@@ -98,14 +110,16 @@ extern "C" int inla_test_profile_read(char* buf, int len) {
   cudaEventSynchronize(last);
   std::map<std::string, std::pair<long, double>> acc;
   for (size_t i = 0; i < g_prof.ev.size(); ++i) {
-    cudaEvent_t next = i + 1 < g_prof.ev.size() ? g_prof.ev[i + 1].first : last;
+    cudaEvent_t next = i + 1 < g_prof.ev.size() ? g_prof.ev[i + 1].ev : last;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, g_prof.ev[i].first, next);
-    auto& a = acc[g_prof.ev[i].second];
+    cudaEventElapsedTime(&ms, g_prof.ev[i].ev, next);
+    const std::string key = by_phase ? std::string(g_prof.ev[i].phase) + "/" + g_prof.ev[i].kernel
+                                     : std::string(g_prof.ev[i].kernel);
+    auto& a = acc[key];
     a.first += 1;
     a.second += ms;
   }
-  for (auto& p : g_prof.ev) cudaEventDestroy(p.first);
+  for (auto& p : g_prof.ev) cudaEventDestroy(p.ev);
   cudaEventDestroy(last);
   g_prof.ev.clear();
   std::vector<std::pair<std::string, std::pair<long, double>>> v(acc.begin(), acc.end());
@@ -118,3 +132,6 @@ extern "C" int inla_test_profile_read(char* buf, int len) {
   }
   return off;
 }
+
+extern "C" int inla_test_profile_read(char* buf, int len) { return profile_read(buf, len, false); }
+extern "C" int inla_test_profile_read_by_phase(char* buf, int len) { return profile_read(buf, len, true); }

@@ -166,3 +166,18 @@ def test_spacetime_one_point():
     m = inla.Model(spec)
     lp, st, xs, vs = inla.eval_batch([m], thetas[:1])
     _check(spec, thetas[:1], lp, st, xs, vs, x_tol=CONSTRAINED_X_TOL, v_rtol=CONSTRAINED_V_RTOL)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_intercept_seen_by_more_than_4096_observations(precision):
+    """m = 6000 observations all load the intercept: its row of A^T and its A^T D A pair have
+    more than 4096 contributions and are reduced by whole blocks (the other rows by one warp
+    each); the results match the oracle like any other model."""
+    spec = synth.spatial_poisson("heavy_intercept", synth.SEED_BASE + 91, 255, 6000, [0.0, np.log(0.2)])
+    thetas = np.array([[0.0, np.log(0.2)], [0.2, np.log(0.3)]])
+    m = inla.Model(spec)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision=precision)
+    if precision == "fp64":
+        _check(spec, thetas, lp, st, xs, vs)
+    else:
+        _check(spec, thetas, lp, st, xs, vs, lp_rtol=1e-3 / 3000.0, x_tol=1e-4, v_rtol=1e-4)
