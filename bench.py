@@ -130,6 +130,26 @@ def _h2d_bytes(spec, thetas):
     return int(b)
 
 
+def _pinned_copy(spec, thetas):
+    """The spec's observation arrays, design, points and the theta batch copied into pinned
+    (page-locked) host buffers."""
+    import dataclasses
+    import torch
+
+    def pin(a):
+        a = np.ascontiguousarray(a)
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0].copy()).dtype, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    from paper_2311_08050_gb300.synth import CSR
+    A = CSR(spec.A.nrows, spec.A.ncols, pin(spec.A.rowptr), pin(spec.A.col), pin(spec.A.val))
+    blocks = [dataclasses.replace(b, points=pin(b.points)) if b.points is not None else b for b in spec.blocks]
+    ps = dataclasses.replace(spec, A=A, y=pin(spec.y), blocks=blocks,
+                             offset=pin(spec.offset) if spec.offset is not None else None)
+    return ps, pin(thetas)
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores, one theta per step (bounded by --ref-budget)."""
     rank, world, _ = _dist_env()
@@ -197,6 +217,16 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    tuned = None
+    if args.precision == "mixed" and args.autotune:
+        # precision rungs calibrated on the FD centre against the six-slice evaluation (warm-up)
+        from paper_2311_08050_gb300 import tune
+        tr = tune.tune_precision(model, thetas[0], stream=sptr)
+        kw.update(tr.opts())
+        args.slices, args.newton_slices, args.prior_slices = tr.slices, tr.newton_slices, tr.prior_slices
+        tuned = {"prior_slices": tr.prior_slices, "slices": tr.slices, "newton_slices": tr.newton_slices,
+                 "errors_vs_six_slices": tr.errors, "tuning_seconds": round(tr.seconds, 2),
+                 "tried": [t["setting"] for t in tr.tried]}
     for _ in range(max(1, args.warmup)):
         lp, st = step()
     assert np.all(st == 0), f"warm-up statuses {st.tolist()}"
@@ -286,7 +316,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": f"bf16 Ozaki slices x{args.slices} (prior, final factor) / x{args.newton_slices} (Newton), "
+           "dtype": f"bf16 Ozaki slices x{args.prior_slices or args.slices} (prior) / x{args.slices} (final factor) / "
+                    f"x{args.newton_slices} (Newton), "
                     "exact fp32 accumulation + df64 storage and diagonal tiles"
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
@@ -295,19 +326,22 @@ def run_ours(args):
                       "prior_slices": args.prior_slices or args.slices,
                       "reuse_below": args.reuse_below or 1e-2, "reuse_shrink": args.reuse_shrink or 0.25,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
-                      "outer_block_tuned": outer_block,
+                      "outer_block_tuned": outer_block, "precision_tuned": tuned,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
            "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
            "kernel_breakdown": breakdown[:12], "phase_breakdown": phases, "phase_kernels": phase_kernels}
     # ---------------- end to end from host buffers ----------------
     if not args.no_e2e:
-        from paper_2311_08050_gb300.synth import ModelSpec  # noqa: F401
+        # the step's inputs (observations, design, points, theta batch) in pinned host memory;
+        # every step uploads them through the C ABI and reads the results back to the host
+        pspec, pthetas = _pinned_copy(spec, thetas)
         e2e_steps = max(1, min(args.steps, 2))
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            m2 = inla.Model(spec)
-            lp2, st2, xs2, vs2 = inla.eval_batch([m2], thetas, precision=args.precision, slices=args.slices,
-                                                 newton_slices=args.newton_slices)
+            m2 = inla.Model(pspec)
+            lp2, st2, xs2, vs2 = inla.eval_batch([m2], pthetas, precision=args.precision, slices=args.slices,
+                                                 newton_slices=args.newton_slices, prior_slices=args.prior_slices,
+                                                 reuse_below=args.reuse_below, reuse_shrink=args.reuse_shrink)
             m2.close()
         t_e2e = time.perf_counter() - t0
         out["e2e"] = {"value": nb * e2e_steps / t_e2e * world, "unit": UNIT,
@@ -446,7 +480,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--slices", type=int, default=5, help="slices of the prior inversion and the factor at the mode")
+    ap.add_argument("--slices", type=int, default=5, help="slices of the factor at the mode")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the given slice counts instead of the autotuned rungs")
     ap.add_argument("--newton-slices", type=int, default=4, help="slices of the Newton-step factorisations")
     ap.add_argument("--prior-slices", type=int, default=0, help="slices of the prior inversion (0: --slices)")
     ap.add_argument("--reuse-below", type=float, default=0.0, help="modified Newton: reuse a factor once steps are "

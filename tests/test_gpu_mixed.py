@@ -273,3 +273,19 @@ def test_fd_batch_followers_start_from_the_centre_mode():
     # both routes converge to the same modes (step tolerance 1e-8)
     for b in range(len(thetas)):
         assert np.max(np.abs(xs[b] - xs0[b])) <= 1e-6 * max(1.0, np.max(np.abs(xs0[b])))
+
+
+def test_precision_autotuner_choice_meets_the_targets_against_the_oracle():
+    """The autotuner calibrates on the model against its own six-slice evaluation (no oracle);
+    its choice must hold the targets against the oracle on every point of the workload, and
+    (at n = 256, where fewer bits suffice) cost no more GEMM passes than the default 5/5/4."""
+    from paper_2311_08050_gb300 import tune
+    spec, thetas = synth.poisson_n256_m1000_5pts()
+    m = inla.Model(spec)
+    tr = tune.tune_precision(m, thetas[0])
+    print("tuned", tr.opts(), tr.errors, [t["setting"] for t in tr.tried])
+    assert (tr.prior_slices, tr.slices, tr.newton_slices) in tune.CANDIDATES
+    passes = lambda S: S * (S + 1) // 2
+    assert passes(tr.prior_slices) + passes(tr.slices) <= passes(5) + passes(5)
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed", **tr.opts())
+    _check(spec, thetas, lp, st, xs, vs)
