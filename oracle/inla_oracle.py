@@ -20,8 +20,9 @@ no blocking or fusion of our own):
 * the Gaussian marginals x_i | theta, y ~ N(x_hat_i, (Q*^-1)_ii) (Appendix A.2.1),
   corrected for the constraints by kriging, and
 * stage 2: the Hessian of log pi~ at theta*, the CCD / grid exploration points and the
-  latent marginals integrated over them (Section 2, Stage 2; Appendix A.2; readings at the
-  end of this file).
+  latent marginals integrated over them (Section 2, Stage 2; Appendix A.2), and
+* the variational Bayes correction of the posterior mean (Appendix A.2.2, Algorithm 2)
+  (readings of both at the end of this file).
 
 Readings of the paper taken here (the paper is silent or garbled on these):
   Newton tolerance 1e-8 in the infinity norm, at most 50 iterations, step halving
@@ -389,3 +390,71 @@ def integrate_marginals(spec, theta_star, neg_hessian, Z, delta):
     mean = w @ X
     var = w @ (Vv + X * X) - mean * mean
     return dict(mean=mean, var=var, weights=w, thetas=thetas, log_post=lp)
+
+
+# ------------------------------------------------------------------------------------
+# Variational Bayes correction of the posterior mean (Appendix A.2.2, Algorithm 2)
+#
+# Readings: the Gaussian posterior keeps the Laplace precision Q* and moves its mean by lambda;
+# lambda minimises E_{x ~ N(mu + lambda, Q*^-1)}[-log pi(y|x)] + 1/2 (mu + lambda)^T Q_p (mu + lambda)
+# (the KLD terms that depend on lambda), the expectation expanded to second order in
+# delta = A lambda around the current mean, so each step solves
+#     Q^c lambda = -c,   c = A^T I'(0) + Q_p mu,   Q^c = Q_p + A^T diag(I''(0)) A
+# (the paper prints "Q^c lambda = c": the minimiser of its own objective carries the minus
+# sign).  I'(0)_i, I''(0)_i are the means of l'(eta), l''(eta), l = -log pi(y_i|eta), under
+# eta ~ N(nu_i, sigma_i^2), nu = A mu + offset, sigma_i^2 = (A Q*^-1 A^T)_ii from the Laplace
+# approximation (fixed), by Gauss-Hermite quadrature with 15 points.  The mean is updated until
+# max |lambda| <= 1e-8 (at most 50 steps).  Models with linear constraints are not covered.
+# ------------------------------------------------------------------------------------
+
+VB_GH_POINTS = 15
+VB_TOL = 1e-8
+VB_MAX = 50
+
+
+def neg_loglik_derivs(spec, eta):
+    """l'(eta), l''(eta) of l = -log pi(y|eta) per observation (Poisson: e^eta - y, e^eta;
+    Gaussian with precision tau: tau (eta - y), tau)."""
+    if spec.likelihood == "poisson":
+        e = np.exp(eta)
+        return e - spec.y[..., None] if eta.ndim == 2 else e - spec.y, e
+    tau = spec.lik_prec
+    y = spec.y[..., None] if eta.ndim == 2 else spec.y
+    return tau * (eta - y), np.full_like(eta, tau)
+
+
+def vb_expected_derivs(spec, nu, sigma2, n_gh=VB_GH_POINTS):
+    """I'(0), I''(0): the means of l', l'' under eta_i ~ N(nu_i, sigma2_i) by Gauss-Hermite
+    quadrature (nodes r_j, weights w_j of the weight e^-r^2): (1 / sqrt(pi)) sum_j w_j
+    l(sqrt(2) sigma_i r_j + nu_i)."""
+    r, w = np.polynomial.hermite.hermgauss(n_gh)
+    eta = nu[:, None] + math.sqrt(2.0) * np.sqrt(sigma2)[:, None] * r[None, :]
+    d1, d2 = neg_loglik_derivs(spec, eta)
+    return d1 @ w / math.sqrt(math.pi), d2 @ w / math.sqrt(math.pi)
+
+
+def vb_mean(spec, theta, n_gh=VB_GH_POINTS, tol=VB_TOL, max_iter=VB_MAX):
+    """Algorithm 2 from the Laplace mode at theta: returns the corrected mean, the iterations,
+    the Laplace result and the linear predictor's variances."""
+    if spec.C is not None:
+        raise ValueError("the variational Bayes correction is defined here for unconstrained models")
+    theta = np.asarray(theta, dtype=np.float64)
+    r = evaluate(spec, theta, want_var=False)
+    As = _A_sparse(spec)
+    Qp, _ = prior_precision(spec, theta)
+    Qstar, _ = newton_system(spec, As, Qp, r["x_hat"])
+    Sigma = spd_inverse(chol(Qstar))
+    A = As.toarray()
+    sigma2 = np.einsum("ij,jk,ik->i", A, Sigma, A)
+    mu = r["x_hat"].copy()
+    it = 0
+    for it in range(1, max_iter + 1):
+        nu = As @ mu + _offset(spec)
+        I1, I2 = vb_expected_derivs(spec, nu, sigma2, n_gh)
+        c = As.T @ I1 + Qp @ mu
+        Qc = Qp + (As.T @ sp.diags(I2) @ As).toarray()
+        lam = sla.cho_solve((chol(Qc), True), -c)
+        mu = mu + lam
+        if np.max(np.abs(lam)) <= tol:
+            break
+    return dict(mean=mu, iters=it, laplace=r, sigma_eta2=sigma2)

@@ -536,3 +536,62 @@ def test_grid_integration_matches_adaptive_quadrature_of_the_closed_forms():
     r = O.integrate_marginals(spec, np.array([th_star]), negH, Z, d)
     assert np.max(np.abs(r["mean"] - mean)) <= 1e-7 * np.max(np.abs(mean))
     assert np.max(np.abs(r["var"] / var - 1.0)) <= 1e-7
+
+
+# ---------------------------------------------------------------------------------
+# variational Bayes mean correction (Algorithm 2)
+# ---------------------------------------------------------------------------------
+
+def test_vb_gauss_hermite_means_match_the_lognormal_closed_form():
+    """For a Poisson likelihood l''(eta) = e^eta, whose mean under N(nu, s^2) is e^(nu + s^2/2)."""
+    spec, _ = synth.poisson_n256_m1000_5pts()
+    rng = np.random.default_rng(8)
+    nu = rng.normal(0.5, 1.0, spec.m)
+    s2 = rng.uniform(0.01, 0.8, spec.m)
+    I1, I2 = O.vb_expected_derivs(spec, nu, s2)
+    closed = np.exp(nu + 0.5 * s2)
+    assert np.max(np.abs(I2 / closed - 1.0)) < 1e-12
+    assert np.max(np.abs(I1 - (closed - spec.y))) < 1e-12 * np.max(closed)
+
+
+def test_vb_correction_vanishes_for_a_gaussian_likelihood():
+    """With a Gaussian likelihood the Laplace mode is the exact posterior mean: c = 0 there, so
+    Algorithm 2 stops after one step of size zero (to rounding)."""
+    spec = _dense_gauss_model(2, with_offset=True)
+    theta = np.array([0.2, np.log(0.3), np.log(0.15), np.log(5.0)])
+    r = O.vb_mean(spec, theta)
+    assert r["iters"] == 1
+    assert np.max(np.abs(r["mean"] - r["laplace"]["x_hat"])) < 1e-12 * max(1.0, np.max(np.abs(r["mean"])))
+
+
+def test_vb_mean_minimises_the_stated_objective_by_brute_force():
+    """Tiny Poisson model: the fixed point of Algorithm 2 is the minimiser of
+    E[-log pi(y|x)] + 1/2 mu^T Q_p mu under x ~ N(mu, Q*^-1) (Q* fixed at the Laplace mode),
+    computed here by scipy with the closed-form lognormal expectation."""
+    rng = np.random.default_rng(12)
+    n, m = 6, 25
+    cols = [np.array(sorted({0, 1 + rng.integers(0, n - 1)})) for _ in range(m)]
+    A = CSR.from_rows(m, n, cols, [np.ones(len(c)) for c in cols])
+    y = rng.poisson(2.0, m).astype(float)
+    pts = rng.uniform(0, 1, (n - 1, 2))
+    blocks = [Block("fixed", 1, prec=1e-3),
+              Block("dense_exp", n - 1, points=pts, theta_sigma=0, theta_range_x=1, theta_range_y=1, nugget=1e-6)]
+    spec = ModelSpec("vb_tiny", n, "poisson", A, y, None, blocks, [("gauss", 0.0, 1.0), ("gauss", 0.0, 1.0)])
+    theta = np.array([-0.2, np.log(0.3)])
+    r = O.vb_mean(spec, theta)
+    Qp, _ = O.prior_precision(spec, theta)
+    Ad = A.to_dense()
+    s2 = r["sigma_eta2"]
+
+    def F(mu):
+        nu = Ad @ mu
+        return float(np.sum(np.exp(nu + 0.5 * s2) - y * nu) + 0.5 * mu @ Qp @ mu)
+
+    def G(mu):
+        nu = Ad @ mu
+        return Ad.T @ (np.exp(nu + 0.5 * s2) - y) + Qp @ mu
+
+    res = so.minimize(F, r["laplace"]["x_hat"], jac=G, method="BFGS", options=dict(gtol=1e-12, maxiter=10000))
+    assert np.max(np.abs(r["mean"] - res.x)) < 1e-7 * max(1.0, np.max(np.abs(res.x)))
+    # the correction is not zero for a Poisson likelihood
+    assert np.max(np.abs(r["mean"] - r["laplace"]["x_hat"])) > 1e-4
