@@ -71,6 +71,9 @@ extern "C" {
 #define INLA_OPT_DEVICE_OUT 1  /* x_hat / mean / var outputs are device pointers */
 #define INLA_OPT_NO_SHARED_START 2  /* INLA_MIXED: every point runs Newton from x = 0 with its
                                        own factorisations (see inla_eval_batch) */
+#define INLA_OPT_VB_MEAN 4  /* the x_hat / mean outputs receive the posterior mean corrected by
+                               variational Bayes (Appendix A.2.2, Algorithm 2; see
+                               inla_eval_batch) instead of the Laplace mode */
 
 typedef struct {
   int32_t kind;                 /* INLA_FACTOR_* */
@@ -158,7 +161,14 @@ int inla_eval_theta(inla_model *model, const double *theta, const inla_opts *opt
  * factor (modified Newton: the gradient is each point's own and exact, so each converges to
  * its own mode to the same step tolerance), taking factorisations of their own only if the
  * steps stop shrinking 4x per iteration.  For the 2t + 1 points of a finite-difference stencil
- * this replaces most Newton-step factorisations.  INLA_OPT_NO_SHARED_START turns it off. */
+ * this replaces most Newton-step factorisations.  INLA_OPT_NO_SHARED_START turns it off.
+ * INLA_OPT_VB_MEAN: after the Laplace approximation (log_post, var unchanged), the mean is
+ * corrected by variational Bayes: with sigma_i^2 = (A Q*^-1 A^T)_ii fixed, each step solves
+ * (Q_p + A^T diag(I''(0)) A) lambda = -(A^T I'(0) + Q_p mu), I'(0), I''(0) the means of the
+ * negative log-likelihood's first and second derivatives under eta_i ~ N((A mu + offset)_i,
+ * sigma_i^2) (15-point Gauss-Hermite), preconditioned by the factor of Q* (same fixed point),
+ * until max |lambda| <= 1e-8 (at most 50 steps; INLA_E_NO_CONVERGENCE for the point otherwise).
+ * Models with constraints (k > 0) are rejected with INLA_E_UNSUPPORTED. */
 int inla_eval_batch(inla_model *const *models, int32_t nmodels, const int32_t *model_of_theta,
                     const double *thetas, int32_t B, const inla_opts *opts,
                     double *log_post, int32_t *status, double *const *x_hat,

@@ -57,6 +57,9 @@ int inla_test_profile_read(char *buf, int len);
  * Newton of the points that start from another point's mode, their factor, and the
  * log-determinants, variances and log pi~); resets and returns the bytes written. */
 int inla_test_phase_read(char *buf, int len);
+/* The n-point Gauss-Hermite rule (weight e^{-x^2}, n <= 32) the variational Bayes correction
+ * uses: nodes ascending, weights summing to sqrt(pi).  Host computation, no GPU needed. */
+int inla_test_gauss_hermite(int32_t n, double *nodes, double *weights);
 /* As inla_test_profile_read, the lines keyed "phase/kernel" (the phase in force at the launch). */
 int inla_test_profile_read_by_phase(char *buf, int len);
 

@@ -454,8 +454,54 @@ static int final_factor(Batch& V) {
 // model: they start from that slot's mode with its final factor (see newton_phase), which for the
 // points of one finite-difference stencil -- theta apart by the FD step -- converges in a few
 // cheap iterations instead of a Newton factorisation per step.
+// Variational Bayes correction of the mean (Appendix A.2.2, Algorithm 2; see vb.cu) for the
+// healthy slots, in place on x: sigma_i^2 of the linear predictor from the inverse factor held
+// in Wk, then steps mu += Q*^-1 (-c) with c = A^T I'(0) + Q_p mu until max |step| <= 1e-8.
+// The variances (t1) are set aside while t1 serves the steps.
+static int vb_correction(Batch& B, const inla_opts& o, int* status) {
+  (void)o;
+  const int NB = B.n;
+  std::vector<double> out;
+  std::vector<int32_t> info;
+  for (int i = 0; i < NB; ++i)
+    if (B.h[i].active) cudaMemcpyAsync(B.h[i].vsave, B.h[i].t1, sizeof(double) * B.h[i].n_pad, cudaMemcpyDeviceToDevice, B.st);
+  launch_vb_prepare(B.d_slots, NB, B.mixed ? 1 : 0, B.max_pairs, B.max_m, B.st);
+  std::vector<int> done(NB, 0);
+  constexpr int kVbMax = 50;
+  constexpr double kVbTol = 1e-8;
+  int rc = INLA_OK;
+  for (int it = 0; it < kVbMax; ++it) {
+    int nact = 0;
+    for (int i = 0; i < NB; ++i) nact += B.h[i].active;
+    if (nact == 0) break;
+    if ((rc = launch_vb_terms(B.d_slots, NB, B.max_m, B.st)) != INLA_OK) break;
+    op_qp_gemv(B, 0);                                   // t1 = Q_p mu
+    launch_gradient(B.d_slots, NB, B.max_n, B.st);      // g = A^T (-I') - Q_p mu = -c
+    if ((rc = solve_llt(B, SEL_L, V_G, V_T2, V_G)) != INLA_OK) break;
+    launch_newton_xu(B.d_slots, NB, B.max_n, B.st);     // xn = mu + step
+    launch_step_norm(B.d_slots, NB, B.max_n, B.st);
+    launch_accept(B.d_slots, NB, B.max_n, B.st);
+    if ((rc = read_outputs(B, out, info)) != INLA_OK) break;
+    for (int i = 0; i < NB; ++i)
+      if (B.h[i].active && out[(size_t)i * SLOT_NOUT + OUT_STEP] <= kVbTol) {
+        done[i] = 1;
+        B.h[i].active = 0;
+      }
+    sync_active(B);
+  }
+  for (int i = 0; i < NB; ++i) {
+    if (B.h[i].active && !done[i] && status[i] == INLA_OK) status[i] = INLA_E_NO_CONVERGENCE;
+    B.h[i].active = status[i] == INLA_OK;
+  }
+  sync_active(B);
+  for (int i = 0; i < NB; ++i)
+    if (B.h[i].active) cudaMemcpyAsync(B.h[i].t1, B.h[i].vsave, sizeof(double) * B.h[i].n_pad, cudaMemcpyDeviceToDevice, B.st);
+  return rc;
+}
+
 static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const inla_opts& o, bool want_var,
                      std::vector<int>& status, std::vector<int>& iters, int nlead, const std::vector<int>& anchor_of) {
+  const bool vb = (o.flags & INLA_OPT_VB_MEAN) != 0;
   const int NB = B.n;
   std::vector<double> out;
   std::vector<int32_t> info;
@@ -552,12 +598,17 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   B.S = B.S_exact;
   op_logdet(B, SEL_L, OUT_LOGDET_Q);
   if (B.max_k > 0) op_logdet(B, SEL_S, OUT_LOGDET_S);
-  if (want_var) INLA_TRY(op_variances(B));
+  if (want_var || vb) INLA_TRY(op_variances(B));
   INLA_TRY(debug_check(B.st, "final variances"));
   launch_assemble(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
   for (int i = 0; i < NB; ++i)
     if (B.h[i].active && (info[2 * i] & INFO_NOT_SPD)) fail_slot(B, status.data(), i, INLA_E_NOT_SPD);
+  if (vb) {
+    sync_active(B);
+    prof_phase("vb_mean");
+    INLA_TRY(vb_correction(B, o, status.data()));
+  }
   return INLA_OK;
 }
 
@@ -612,6 +663,8 @@ int logdet_spd_device(const std::vector<double>& Mhost, int k, double* result) {
 struct Layout {
   int np, ndp, kp, m, S;
   bool mixed, want_var;
+  int64_t npairs = 0;   // variational Bayes: the largest A^T A pair count of the group
+  bool vb = false;
 };
 
 // carve the group's workspace (uniform strides); returns the bytes used
@@ -639,8 +692,9 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
     kv1 = cv.take<double>(G * kp);
     kv2 = cv.take<double>(G * kp);
   }
-  double* vecs = cv.take<double>(G * np * 6);
-  double* mvecs = cv.take<double>(G * m * 2);
+  double* vecs = cv.take<double>(G * np * 7);
+  double* mvecs = cv.take<double>(G * m * (L.vb ? 3 : 2));
+  double* pcov = L.vb ? cv.take<double>(G * std::max<int64_t>(L.npairs, 1)) : nullptr;
   double* red = cv.take<double>(G * 256);
   double* outs = cv.take<double>(G * SLOT_NOUT);
   int32_t* infos = cv.take<int32_t>(G * 2);
@@ -682,15 +736,20 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
       s.kv2 = kv2 + i * kp;
     }
     if (vecs) {
-      double* v = vecs + i * np * 6;
+      double* v = vecs + i * np * 7;
       s.x = v;
       s.xn = v + np;
       s.g = v + 2 * np;
       s.t1 = v + 3 * np;
       s.t2 = v + 4 * np;
       s.vd = v + 5 * np;
-      s.eta = mvecs + i * m * 2;
+      s.vsave = v + 6 * np;
+      s.eta = mvecs + i * m * (L.vb ? 3 : 2);
       s.w = s.eta + m;
+      if (L.vb) {
+        s.etav = s.eta + 2 * m;
+        s.pcov = pcov + i * std::max<int64_t>(L.npairs, 1);
+      }
       s.red = red + i * 256;
       s.out = outs + i * SLOT_NOUT;
       s.info = infos + i * 2;
@@ -727,6 +786,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
   const bool want_var = var != nullptr;
+  const bool vb = (o.flags & INLA_OPT_VB_MEAN) != 0;
   int theta_dim = -1;
   std::vector<int> mi_of(B_);
   for (int b = 0; b < B_; ++b) {
@@ -738,6 +798,9 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   }
   for (int64_t i = 0; i < (int64_t)B_ * theta_dim; ++i)
     if (!std::isfinite(thetas[i])) return INLA_E_BADARG;
+  if (vb)
+    for (int b = 0; b < B_; ++b)
+      if (models[mi_of[b]]->d.k > 0) return INLA_E_UNSUPPORTED;  // variational Bayes: no constraints
   int device = 0;
   INLA_CUDA_TRY(cudaGetDevice(&device));
   std::lock_guard<std::mutex> lock(g_mutex);
@@ -752,6 +815,8 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   for (auto& kv : groups) {
     const ModelDev& d = models[mi_of[kv.second[0]]]->d;
     Layout L{d.n_pad, d.nd_pad, d.k_pad, d.m, S, mixed, want_var};
+    L.vb = vb;
+    for (int b : kv.second) L.npairs = std::max(L.npairs, models[mi_of[b]]->d.npairs);
     Carve cv(nullptr);
     Batch Bt;
     std::vector<Slot> h;
@@ -814,6 +879,8 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     const int G = (int)idx.size();
     const ModelDev& d0 = models[mi_of[idx[0]]]->d;
     Layout L{d0.n_pad, d0.nd_pad, d0.k_pad, d0.m, S, mixed, want_var};
+    L.vb = vb;
+    for (int b : idx) L.npairs = std::max(L.npairs, models[mi_of[b]]->d.npairs);
     Carve cv(g_arena.base);
     Batch Bt;
     carve_group(cv, L, G, Bt, Bt.h);

@@ -84,6 +84,9 @@ struct ModelDev {
   int32_t n_heavy_cols, n_heavy_pairs;
   int32_t* heavy_cols;
   int64_t* heavy_pairs;
+  // per observation i, the pairs (k, l) of its A row and a_ik a_il (twice for k != l): the
+  // variance of eta_i is sum over them of coef * (Q*^-1)_kl
+  int64_t* obs_ptr; int32_t* obs_pair; double* obs_coef;
   int32_t *pc_obs; double *pc_coef;                        // contributions
   double *y, *offset;                                      // offset may be null
   double lgamma_sum;                                       // sum log y! (Poisson)
@@ -134,7 +137,10 @@ struct Slot {
   // vectors
   double *x, *xn, *g, *t1, *t2;    // n_pad
   double *vd;                      // n_pad: double-float copy of a vector (mixed path)
+  double *vsave;                   // n_pad: the variances while the variational Bayes steps run
   double *eta, *w;                 // m
+  double *etav;                    // m: variance of the linear predictor (variational Bayes)
+  double *pcov;                    // unique A^T A pairs: (Q*^-1)_kl (variational Bayes)
   double *kv1, *kv2;               // k_pad
   double *red;                     // reduction scratch (256 doubles)
   double *out;                     // scalar outputs (SLOT_NOUT doubles)

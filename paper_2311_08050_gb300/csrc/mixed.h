@@ -68,6 +68,11 @@ struct Batch {
   int64_t spin_limit;
 };
 
+// variational Bayes mean correction (vb.cu): (Q*^-1)_kl for the A^T A pairs and the linear
+// predictor's variances (needs the inverse factor in Wk); the correction's residual and weights
+void launch_vb_prepare(Slot* slots, int nslots, int mixed, int64_t max_pairs, int max_m, cudaStream_t st);
+int launch_vb_terms(Slot* slots, int nslots, int max_m, cudaStream_t st);
+
 // mixed blocked routines (eval_mixed.cu)
 int mixed_potrf(Batch& B, int sel);          // replays a captured CUDA graph for a known layout
 void mixed_graphs_clear();                   // drop every captured graph (workspace reallocated)

@@ -289,6 +289,20 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
     if (pptr[q + 1] - pptr[q] > HEAVY_LEN) heavy_pairs.push_back(q);
   d.n_heavy_cols = (int32_t)heavy_cols.size();
   d.n_heavy_pairs = (int32_t)heavy_pairs.size();
+  std::vector<int64_t> optr((size_t)m + 1, 0);
+  for (size_t c = 0; c < con.size(); ++c) optr[(size_t)con[c].obs + 1]++;
+  for (int i = 0; i < m; ++i) optr[i + 1] += optr[i];
+  std::vector<int32_t> opair(con.size());
+  std::vector<double> ocoef(con.size());
+  {
+    std::vector<int64_t> fill(optr.begin(), optr.end() - 1);
+    for (int64_t q = 0; q < d.npairs; ++q)
+      for (int64_t c = pptr[q]; c < pptr[q + 1]; ++c) {
+        const int64_t at = fill[pobs[c]]++;
+        opair[at] = (int32_t)q;
+        ocoef[at] = pcoef[c] * (prow[q] != pcol[q] ? 2.0 : 1.0);
+      }
+  }
   if (D->likelihood == INLA_LIK_POISSON) {
     double s = 0.0;
     for (int i = 0; i < m; ++i) s += std::lgamma(D->y[i] + 1.0);
@@ -452,6 +466,9 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   INLA_TRY(dev_copy(M, &d.pc_obs, pobs.data(), pobs.size()));
   INLA_TRY(dev_copy(M, &d.pc_coef, pcoef.data(), pcoef.size()));
   INLA_TRY(dev_copy(M, &d.heavy_cols, heavy_cols.data(), heavy_cols.size()));
+  INLA_TRY(dev_copy(M, &d.obs_ptr, optr.data(), optr.size()));
+  INLA_TRY(dev_copy(M, &d.obs_pair, opair.data(), opair.size()));
+  INLA_TRY(dev_copy(M, &d.obs_coef, ocoef.data(), ocoef.size()));
   INLA_TRY(dev_copy(M, &d.heavy_pairs, heavy_pairs.data(), heavy_pairs.size()));
   INLA_TRY(dev_copy(M, &d.y, D->y, (size_t)m));
   if (D->offset) INLA_TRY(dev_copy(M, &d.offset, D->offset, (size_t)m));

@@ -23,6 +23,7 @@ PRIOR = {"gauss": 0, "pc_prec": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 OPT_DEVICE_OUT = 1
 OPT_NO_SHARED_START = 2
+OPT_VB_MEAN = 4
 
 EXPORTED = ["inla_opts_default", "inla_model_create", "inla_model_destroy", "inla_eval_theta",
             "inla_eval_batch", "inla_marginals", "inla_status_string"]
