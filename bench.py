@@ -473,6 +473,94 @@ def run_surrogate(args):
     print(json.dumps({"surrogate_experiment": res}), flush=True)
 
 
+_ORACLE_TIMER = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+from paper_2311_08050_gb300 import synth
+from oracle import inla_oracle as O
+w = synth.WORKLOADS[sys.argv[2]]()
+specs, thetas = w
+if not isinstance(specs, list):
+    specs = [specs] * len(thetas)
+k = int(sys.argv[3])
+t0 = time.perf_counter()
+for b in range(k):
+    O.evaluate(specs[b], thetas[b])
+print(json.dumps({"seconds": time.perf_counter() - t0, "points": k}))
+"""
+
+
+def _time_oracle(workload, points, cores):
+    """The oracle on `points` theta points of a workload in a child process limited to `cores`
+    BLAS / OpenMP threads (None: all host cores)."""
+    env = dict(os.environ)
+    if cores:
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[v] = str(cores)
+    r = subprocess.run([sys.executable, "-c", _ORACLE_TIMER, ROOT, workload, str(points)], capture_output=True,
+                       text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip()[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"theta_evals_per_s": d["points"] / d["seconds"], "points": d["points"], "seconds": d["seconds"],
+            "cores": cores or os.cpu_count()}
+
+
+def run_configs(args):
+    """theta-evals/s of every workload of the scope table: the GPU mixed path (precision tuned
+    per workload) and FP64 path on the whole batch (or the first points at n >= 8192), and the
+    FP64 oracle on the host cores (all cores; one core where a point takes at most a minute)."""
+    import torch
+    from paper_2311_08050_gb300 import build as B
+    from paper_2311_08050_gb300 import inla, synth, tune
+    B.build()
+    torch.cuda.set_device(0)
+    rows = []
+    plan = [("poisson_n256_m1000_5pts", 5, 5, 5, 5), ("poisson_n4096_m20000_fd7", 7, 7, 2, 1),
+            ("spacetime_n8149_m8000_fd13", 13, 1, 1, 0), ("gaussian_64_models_n512_4096", 64, 64, 8, 4),
+            ("poisson_n16384_m100000_fd9", 9, 1, 1, 0)]
+    for name, n_mixed, n_fp64, n_orc, n_orc1 in plan:
+        specs, thetas = synth.WORKLOADS[name]()
+        multi = isinstance(specs, list)
+        models = [inla.Model(s) for s in specs] if multi else [inla.Model(specs)]
+        mot = np.arange(len(models), dtype=np.int32) if multi else None
+
+        def run(k, **kw):
+            sub = thetas[:k]
+            return inla.eval_batch(models, sub, model_of_theta=None if mot is None else mot[:k], **kw)
+
+        row = {"workload": name, "batch": len(thetas)}
+        tuned = tune.tune_precision(models[0], thetas[0]) if not multi else None
+        kw = tuned.opts() if tuned else {}
+        run(n_mixed, precision="mixed", **kw)  # warm-up (outer-block tuner, graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lp, st, _, _ = run(n_mixed, precision="mixed", **kw)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        row["gpu_mixed"] = {"theta_evals_per_s": n_mixed / tm, "points": n_mixed, "seconds": tm,
+                            "statuses_ok": bool(np.all(st == 0)),
+                            "slices": tuned.opts() if tuned else "5/5/4 (default; 64 models, not tuned)"}
+        if n_fp64 > 1:
+            run(min(n_fp64, 2), precision="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lp64, st64, _, _ = run(n_fp64, precision="fp64")
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        row["gpu_fp64"] = {"theta_evals_per_s": n_fp64 / t64, "points": n_fp64, "seconds": t64,
+                           "statuses_ok": bool(np.all(st64 == 0))}
+        row["mixed_minus_fp64_log_post_max"] = float(np.max(np.abs(lp[:n_fp64] - lp64))) if n_fp64 <= n_mixed else None
+        row["oracle_all_cores"] = _time_oracle(name, n_orc, None)
+        if n_orc1:
+            row["oracle_one_core"] = _time_oracle(name, n_orc1, 1)
+        for m in models:
+            m.close()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"configs": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,6 +585,8 @@ def main():
                     help="the benchmark workload (default) or a smaller case for profiling captures")
     ap.add_argument("--gemm", default=None, help="microbenchmark the Ozaki GEMM: 'M,N,K,S[,lower[,accumulate]];...'")
     ap.add_argument("--surrogate", action="store_true", help="the learned-surrogate experiment (time to the mode)")
+    ap.add_argument("--configs", action="store_true", help="theta-evals/s of every workload: GPU mixed, GPU FP64, "
+                    "oracle on all host cores and on one")
     ap.add_argument("--train", type=int, default=2000, help="--surrogate: exact training evaluations")
     ap.add_argument("--holdout", type=int, default=200, help="--surrogate: held-out exact evaluations")
     ap.add_argument("--surrogate-batch", type=int, default=16, help="--surrogate: points per batched call")
@@ -506,6 +596,9 @@ def main():
         return
     if args.surrogate:
         run_surrogate(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -21,8 +21,9 @@ no blocking or fusion of our own):
   corrected for the constraints by kriging, and
 * stage 2: the Hessian of log pi~ at theta*, the CCD / grid exploration points and the
   latent marginals integrated over them (Section 2, Stage 2; Appendix A.2), and
-* the variational Bayes correction of the posterior mean (Appendix A.2.2, Algorithm 2)
-  (readings of both at the end of this file).
+* the variational Bayes correction of the posterior mean (Appendix A.2.2, Algorithm 2), and
+* the Moore-Penrose / Woodbury covariance route of Section 3.1, Eq. (woodeqn)
+  (readings of these at the end of this file).
 
 Readings of the paper taken here (the paper is silent or garbled on these):
   Newton tolerance 1e-8 in the infinity norm, at most 50 iterations, step halving
@@ -458,3 +459,53 @@ def vb_mean(spec, theta, n_gh=VB_GH_POINTS, tol=VB_TOL, max_iter=VB_MAX):
         if np.max(np.abs(lam)) <= tol:
             break
     return dict(mean=mu, iters=it, laplace=r, sigma_eta2=sigma2)
+
+
+# ------------------------------------------------------------------------------------
+# Moore-Penrose / Woodbury covariance route (Section 3.1, Eq. (woodeqn); Appendix C)
+#
+# Q+ is the Moore-Penrose pseudo-inverse of the prior precision without the eps jitter (block
+# by block: 1 / prec, 1 / tau, the dense covariance Sigma, and (tau R)+ for intrinsic blocks);
+# the posterior covariance is Sigma* = Q+ - Q+ (I + Q_like Q+)^-1 Q_like Q+ with
+# Q_like = A^T D A the likelihood's negative Hessian.  Reading: Q_like is taken at the mode of
+# the kriging route (with eps), to which this route is equal as eps -> 0 (Appendix C).
+# ------------------------------------------------------------------------------------
+
+def prior_pseudo_inverse(spec, theta):
+    """Q+ block by block (dense n x n)."""
+    n = spec.n
+    P = np.zeros((n, n))
+    start = 0
+    for blk in spec.blocks:
+        sl = slice(start, start + blk.size)
+        if blk.kind == "fixed":
+            P[sl, sl] = np.eye(blk.size) / blk.prec
+        elif blk.kind == "iid":
+            P[sl, sl] = np.eye(blk.size) * math.exp(-theta[blk.theta_idx])
+        elif blk.kind == "dense_exp":
+            P[sl, sl] = exp_covariance(blk, theta)
+        elif blk.kind == "kron":
+            R = np.ones((1, 1))
+            for f in blk.factors:
+                R = np.kron(R, structure_matrix(f))
+            P[sl, sl] = np.linalg.pinv(math.exp(theta[blk.theta_idx]) * R, rcond=1e-10, hermitian=True)
+        start += blk.size
+    return P
+
+
+def woodbury_covariance(Qplus, Qlike):
+    """Eq. (woodeqn): Q+ - Q+ (I + Q_like Q+)^-1 Q_like Q+."""
+    n = Qplus.shape[0]
+    return Qplus - Qplus @ np.linalg.solve(np.eye(n) + Qlike @ Qplus, Qlike @ Qplus)
+
+
+def woodbury_marginals(spec, theta):
+    """Mean (the kriging route's mode) and the marginal variances of Eq. (woodeqn)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    r = evaluate(spec, theta, want_var=False)
+    As = _A_sparse(spec)
+    eta = As @ r["x_hat"] + _offset(spec)
+    w = np.exp(eta) if spec.likelihood == "poisson" else np.full(spec.m, spec.lik_prec)
+    Qlike = (As.T @ sp.diags(w) @ As).toarray()
+    S = woodbury_covariance(prior_pseudo_inverse(spec, theta), Qlike)
+    return dict(mean=r["x_hat"], var=np.diag(S), laplace=r)

@@ -206,19 +206,19 @@ __global__ void k_s_pad_identity(Slot* slots) {
 }
 
 // Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
-// GPU's FP64 rate is ~2 FMA/clock/SM).  One CTA of 1024 threads per tile, the tile in shared
+// GPU's FP64 rate is ~2 FMA/clock/SM).  One CTA of DG_THREADS threads per tile, the tile in shared
 // memory (row pitch 65 cells).  Factor: right-looking elimination A = L1 D L1^T, step j
 // subtracting (a_ij / a_jj) a_cj from every a_ic with i >= c > j.  The elements of step j are the
 // first (63 - j)(64 - j) / 2 entries of a fixed table that lists the lower triangle by column,
-// last column first, so the threads share each step evenly (at most two elements each, skipped
-// uniformly when absent); thread 0 only updates the next pivot a_{j+1,j+1} and publishes its
+// last column first, so the threads share each step evenly (at most a few elements each, the
+// absent ones skipped uniformly); thread 0 only updates the next pivot a_{j+1,j+1} and publishes its
 // reciprocal, so one barrier per step closes it.  Then L = L1 D^1/2 is written out and L1 is
 // inverted in place by levels (s = 1, 2, .., 32: two inverted diagonal blocks of size s and the
 // block below them give the inverse of the 2s block, -Y22 L21 Y11), so L^-1 = D^-1/2 Y.  Stores
 // the factor tile (double-float, upper part zeroed) and the inverse tile (double-float, in the
 // FP64-sized cells of the inverse-tile array).
 constexpr int DG_LD = TB + 1;
-constexpr int DG_THREADS = 1024;
+constexpr int DG_THREADS = 512;
 __device__ __forceinline__ df dg_ld(const float2* t, int i, int c) { return df_make(t[i * DG_LD + c].x, t[i * DG_LD + c].y); }
 __device__ __forceinline__ void dg_st(float2* t, int i, int c, df v) { t[i * DG_LD + c] = make_float2(v.hi, v.lo); }
 
@@ -273,35 +273,32 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
       dg_st(t, j + 1, j + 1, v);
       pivot_recip(v, j + 1);
     } else {
-      // elements (tid - 1) and (tid - 1) + NW of the step's list without its pivot
-      int e0 = tid - 1, e1 = tid - 1 + NW;
-      e0 += e0 >= pidx;
-      e1 += e1 >= pidx;
-      const bool h0 = e0 < cnt, h1 = e1 < cnt;
-      df a0, u0, b0, a1, u1, b1;
-      int p0 = 0, p1 = 0;
-      if (h0) {
-        const int ic = tab[e0], i = ic >> 8, c = ic & 255;
-        p0 = i * DG_LD + c;
-        a0 = dg_ld(t, i, c);
-        u0 = dg_ld(t, i, j);
-        b0 = dg_ld(t, c, j);
+      // elements (tid - 1) + NW q of the step's list without its pivot, all loaded first
+      constexpr int EPT = (NTRI - TB + NW - 1) / NW;
+      const int nq = (cnt - 1 + NW - 1) / NW;  // block-uniform
+      df a[EPT], u[EPT], b[EPT];
+      int pos[EPT];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        pos[q] = -1;
+        if (q < nq) {
+          int e = tid - 1 + NW * q;
+          e += e >= pidx;
+          if (e < cnt) {
+            const int ic = tab[e], i = ic >> 8, c = ic & 255;
+            pos[q] = i * DG_LD + c;
+            a[q] = dg_ld(t, i, c);
+            u[q] = dg_ld(t, i, j);
+            b[q] = dg_ld(t, c, j);
+          }
+        }
       }
-      if (h1) {
-        const int ic = tab[e1], i = ic >> 8, c = ic & 255;
-        p1 = i * DG_LD + c;
-        a1 = dg_ld(t, i, c);
-        u1 = dg_ld(t, i, j);
-        b1 = dg_ld(t, c, j);
-      }
-      if (h0) {
-        const df v = df_add_fast(a0, df_neg(df_mul(df_mul(u0, r), b0)));
-        t[p0] = make_float2(v.hi, v.lo);
-      }
-      if (h1) {
-        const df v = df_add_fast(a1, df_neg(df_mul(df_mul(u1, r), b1)));
-        t[p1] = make_float2(v.hi, v.lo);
-      }
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (q < nq && pos[q] >= 0) {
+          const df v = df_add_fast(a[q], df_neg(df_mul(df_mul(u[q], r), b[q])));
+          t[pos[q]] = make_float2(v.hi, v.lo);
+        }
     }
     __syncthreads();
   }
@@ -327,35 +324,58 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     else if (c == i) v = df_make(dsq[i].x, dsq[i].y);
     base[(size_t)i * M.ld + c] = make_float2(v.hi, v.lo);
   }
-  // ---- Y = L1^-1 in place, level by level (unit diagonal implicit); one output per thread:
-  // level s has 64 / (2 s) blocks of s x s outputs, 32 s in all ----
+  // ---- Y = L1^-1 in place, level by level (unit diagonal implicit); level s has 64 / (2 s)
+  // blocks of s x s outputs, 32 s in all, OPT = 1024 / DG_THREADS of them per thread at most ----
+  constexpr int OPT = (32 * 32 + DG_THREADS - 1) / DG_THREADS;
   for (int sz = 1; sz < TB; sz <<= 1) {
     const int lg = __ffs(sz) - 1;          // sz = 2^lg
-    const bool on = tid < 32 * sz;
-    int row = 0, p = 0, c = 0, r = 0;
-    if (on) {
-      const int blk = tid >> (2 * lg), rem = tid & (sz * sz - 1);
-      r = rem >> lg;
-      c = rem & (sz - 1);
-      p = blk * 2 * sz;
-      row = p + sz + r;
-    }
-    df tv;
+    const int nel = 32 * sz;
+    df tv[OPT];
     // T = L21 Y11: T_rc = L21_rc + sum_{k = c+1}^{sz-1} L21_rk Y11_kc
-    if (on) {
-      tv = dg_ld(t, row, p + c);
-      for (int k = c + 1; k < sz; ++k) tv = df_add_fast(tv, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int e = tid + DG_THREADS * q;
+      if (e < nel) {
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int p = blk * 2 * sz, row = p + sz + r;
+        df acc = dg_ld(t, row, p + c);
+        for (int k = c + 1; k < sz; ++k) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
+        tv[q] = acc;
+      }
     }
     __syncthreads();
-    if (on) dg_st(t, row, p + c, tv);
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int e = tid + DG_THREADS * q;
+      if (e < nel) {
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int p = blk * 2 * sz;
+        dg_st(t, p + sz + r, p + c, tv[q]);
+      }
+    }
     __syncthreads();
     // Y21 = -Y22 T: -(T_rc + sum_{k < r} Y22_rk T_kc)
-    if (on) {
-      tv = dg_ld(t, row, p + c);
-      for (int k = 0; k < r; ++k) tv = df_add_fast(tv, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int e = tid + DG_THREADS * q;
+      if (e < nel) {
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int p = blk * 2 * sz, row = p + sz + r;
+        df acc = dg_ld(t, row, p + c);
+        for (int k = 0; k < r; ++k) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
+        tv[q] = df_neg(acc);
+      }
     }
     __syncthreads();
-    if (on) dg_st(t, row, p + c, df_neg(tv));
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int e = tid + DG_THREADS * q;
+      if (e < nel) {
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int p = blk * 2 * sz;
+        dg_st(t, p + sz + r, p + c, tv[q]);
+      }
+    }
     __syncthreads();
   }
   // ---- L^-1 = D^-1/2 Y ----

@@ -595,3 +595,27 @@ def test_vb_mean_minimises_the_stated_objective_by_brute_force():
     assert np.max(np.abs(r["mean"] - res.x)) < 1e-7 * max(1.0, np.max(np.abs(res.x)))
     # the correction is not zero for a Poisson likelihood
     assert np.max(np.abs(r["mean"] - r["laplace"]["x_hat"])) > 1e-4
+
+
+# ---------------------------------------------------------------------------------
+# Moore-Penrose / Woodbury route (Section 3.1, Eq. (woodeqn))
+# ---------------------------------------------------------------------------------
+
+def test_woodbury_route_reproduces_appendix_c_and_the_kriging_limit():
+    """The oracle's Eq. (woodeqn) on Appendix C's printed inputs gives the printed Sigma*; its
+    pseudo-inverse of RW1(4) is the printed Q_e+; and on a constrained model its variances equal
+    the kriging route's as eps -> 0 (eps = 1e-9 here: relative differences ~1e-6)."""
+    g = _read_golden("appendix_c_example.txt")
+    A, Ql, Qe = g["A"], np.diag(g["Ql"]), g["Qe"]
+    P = np.linalg.pinv(Qe, hermitian=True)
+    assert np.max(np.abs(P - g["Qe_pinv"])) <= 5e-4
+    S = O.woodbury_covariance(P, A.T @ Ql @ A)
+    assert np.max(np.abs(S - g["Sigma_star"])) <= 5e-4
+    spec = _structured_model(3, "poisson")
+    for blk in spec.blocks:
+        if blk.kind == "kron":
+            blk.eps = 1e-9
+    theta = np.array([0.5, 1.0, -0.3, 0.8])
+    wb = O.woodbury_marginals(spec, theta)
+    kr = O.evaluate(spec, theta)
+    assert np.max(np.abs(wb["var"] / kr["var"] - 1.0)) < 1e-5
