@@ -74,6 +74,8 @@ extern "C" {
 #define INLA_OPT_VB_MEAN 4  /* the x_hat / mean outputs receive the posterior mean corrected by
                                variational Bayes (Appendix A.2.2, Algorithm 2; see
                                inla_eval_batch) instead of the Laplace mode */
+#define INLA_OPT_WOODBURY_VAR 8  /* INLA_MIXED: the var outputs by the Moore-Penrose / Woodbury
+                               route of Section 3.1, Eq. (woodeqn) (see inla_eval_batch) */
 
 typedef struct {
   int32_t kind;                 /* INLA_FACTOR_* */
@@ -168,7 +170,15 @@ int inla_eval_theta(inla_model *model, const double *theta, const inla_opts *opt
  * negative log-likelihood's first and second derivatives under eta_i ~ N((A mu + offset)_i,
  * sigma_i^2) (15-point Gauss-Hermite), preconditioned by the factor of Q* (same fixed point),
  * until max |lambda| <= 1e-8 (at most 50 steps; INLA_E_NO_CONVERGENCE for the point otherwise).
- * Models with constraints (k > 0) are rejected with INLA_E_UNSUPPORTED. */
+ * Models with constraints (k > 0) are rejected with INLA_E_UNSUPPORTED.
+ * INLA_OPT_WOODBURY_VAR (INLA_MIXED only): the marginal variances are taken from
+ * Sigma* = Q+ - Q+ (I + Q_like Q+)^-1 Q_like Q+, Q+ the Moore-Penrose pseudo-inverse of the prior
+ * precision without the eps jitter of intrinsic blocks (block by block: 1 / prec, exp(-theta),
+ * the dense covariance, and the Kronecker product of the factors' pseudo-inverses over tau), and
+ * Q_like = A^T D A at the mode of the kriging route -- evaluated in the symmetric form
+ * Q+ - Q+ B^T (I + B Q+ B^T)^-1 B Q+, B = D^1/2 A, whose m x m system needs round_up(m, 256) <=
+ * the padded n (INLA_E_UNSUPPORTED otherwise, and with INLA_FP64 or INLA_OPT_VB_MEAN).  As eps -> 0
+ * the two routes agree; log_post and x_hat are those of the kriging route. */
 int inla_eval_batch(inla_model *const *models, int32_t nmodels, const int32_t *model_of_theta,
                     const double *thetas, int32_t B, const inla_opts *opts,
                     double *log_post, int32_t *status, double *const *x_hat,

@@ -598,7 +598,11 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   B.S = B.S_exact;
   op_logdet(B, SEL_L, OUT_LOGDET_Q);
   if (B.max_k > 0) op_logdet(B, SEL_S, OUT_LOGDET_S);
-  if (want_var || vb) INLA_TRY(op_variances(B));
+  if (o.flags & INLA_OPT_WOODBURY_VAR) {
+    if (want_var) INLA_TRY(mixed_woodbury_variances(B));
+  } else if (want_var || vb) {
+    INLA_TRY(op_variances(B));
+  }
   INLA_TRY(debug_check(B.st, "final variances"));
   launch_assemble(B.d_slots, NB, B.st);
   INLA_TRY(read_outputs(B, out, info));
@@ -801,6 +805,15 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   if (vb)
     for (int b = 0; b < B_; ++b)
       if (models[mi_of[b]]->d.k > 0) return INLA_E_UNSUPPORTED;  // variational Bayes: no constraints
+  if (o.flags & INLA_OPT_WOODBURY_VAR) {
+    // the Moore-Penrose route: mixed path, its m x m system inside the slot's n_pad x n_pad
+    // buffers, and not with the variational Bayes correction (which needs the inverse factor)
+    if (!mixed || vb) return INLA_E_UNSUPPORTED;
+    for (int b = 0; b < B_; ++b) {
+      const ModelDev& d = models[mi_of[b]]->d;
+      if (round_up(std::max(d.m, 1), PAD) > d.n_pad) return INLA_E_UNSUPPORTED;
+    }
+  }
   int device = 0;
   INLA_CUDA_TRY(cudaGetDevice(&device));
   std::lock_guard<std::mutex> lock(g_mutex);
@@ -914,6 +927,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
       s.nd = d.nd;
       s.nd_pad = d.nd_pad;
       s.nd_off = d.nd_off;
+      s.aux_n = (int32_t)round_up(std::max(d.m, 1), PAD);
       s.active = 1;
       for (int t = 0; t < theta_dim; ++t) s.theta[t] = thetas[(size_t)b * theta_dim + t];
       Bt.max_entries = std::max(Bt.max_entries, d.nentries);

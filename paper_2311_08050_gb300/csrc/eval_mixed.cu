@@ -30,6 +30,7 @@ MRef mref(const Batch& B, int sel) {
   const Slot& s = B.h[0];
   if (sel == SEL_L) return MRef{reinterpret_cast<float2*>(s.L), B.mat_stride, B.np, B.np, s.Linv, B.linv_stride, sel};
   if (sel == SEL_COV) return MRef{reinterpret_cast<float2*>(s.Wk), B.mat_stride, B.ndp, B.np, s.Wd, B.wd_stride, sel};
+  if (sel == SEL_AUX) return MRef{reinterpret_cast<float2*>(s.Qp), B.mat_stride, s.aux_n, B.np, s.Linv, B.linv_stride, sel};
   return MRef{reinterpret_cast<float2*>(s.S), B.s_stride, B.kp, B.kp, s.SLinv, B.slinv_stride, sel};
 }
 
@@ -414,6 +415,21 @@ int mixed_var_constraint(Batch& B) {
   INLA_TRY(oz_gemm(pz, pw, a, B.n, B.st));
   INLA_TRY(trsm_left(B, SEL_S, G, B.mat_stride, B.np, B.np, false));
   launch_colsumsq_gt_df(B.d_slots, B.n, B.np / TB, B.st);
+  return INLA_OK;
+}
+
+// Marginal variances by the Moore-Penrose / Woodbury route (Section 3.1, Eq. (woodeqn)) in its
+// symmetric m x m form: with B = D^1/2 A (D the likelihood weights at the mode),
+//   Sigma* = Q+ - Q+ B^T (I + B Q+ B^T)^-1 B Q+,
+// so diag(Sigma*)_j = Q+_jj - |L_M^-1 (B Q+)_{:,j}|^2 with L_M the factor of M = I + B Q+ B^T.
+// Q+ (block pseudo-inverse of the prior precision) in Wk, G = B Q+ in L (rows [0, m)), M in Qp
+// (aux_n x aux_n), its factor by the mixed Cholesky, Z = L_M^-1 G by forward substitution, the
+// variances into t1.  Needs aux_n <= n_pad.
+int mixed_woodbury_variances(Batch& B) {
+  launch_woodbury_terms_df(B.d_slots, B.n, B.np, B.st);
+  INLA_TRY(mixed_potrf(B, SEL_AUX));
+  INLA_TRY(trsm_left(B, SEL_AUX, reinterpret_cast<float2*>(B.h[0].L), B.mat_stride, B.np, B.np, false));
+  launch_woodbury_var_df(B.d_slots, B.n, B.np, B.st);
   return INLA_OK;
 }
 

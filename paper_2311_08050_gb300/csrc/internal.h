@@ -67,6 +67,18 @@ struct KronLogdet {
   double eps;
 };
 
+// A prior block in internal order (the Moore-Penrose route builds the pseudo-inverse of the
+// prior precision block by block): INLA_BLOCK_* kind, internal offset and size, its theta index
+// (-1 for a fixed block), the fixed precision, and for Kronecker blocks the factors' sizes and
+// the offsets of their pseudo-inverses (row-major) in ModelDev::factor_pinv.
+constexpr int MAX_BLOCKS = 16;
+struct BlockInfo {
+  int32_t kind, off, size, theta_idx;
+  double prec;
+  int32_t nf, fsize[3];
+  int64_t pinv_off[3];
+};
+
 // Device-resident, theta-independent model data.
 struct ModelDev {
   int32_t n, n_pad, m, k, k_pad, nd, nd_pad;   // nd: dense block size (0 if none)
@@ -87,6 +99,9 @@ struct ModelDev {
   // per observation i, the pairs (k, l) of its A row and a_ik a_il (twice for k != l): the
   // variance of eta_i is sum over them of coef * (Q*^-1)_kl
   int64_t* obs_ptr; int32_t* obs_pair; double* obs_coef;
+  int32_t nblk;
+  BlockInfo blk[MAX_BLOCKS];
+  double* factor_pinv;
   int32_t *pc_obs; double *pc_coef;                        // contributions
   double *y, *offset;                                      // offset may be null
   double lgamma_sum;                                       // sum log y! (Poisson)
@@ -147,6 +162,7 @@ struct Slot {
   int32_t *info;                   // [0] status flags, [1] failing pivot
   const ModelDev *md;              // device copy of the model struct
   int32_t n_pad, n, m, k, k_pad, nd, nd_pad, nd_off;
+  int32_t aux_n;                   // padded size of the Moore-Penrose route's m x m system
   int32_t active;                 // participates in the current Newton step
   double theta[MAX_THETA];
 };

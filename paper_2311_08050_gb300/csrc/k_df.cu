@@ -20,6 +20,7 @@ struct DfRef {
 __device__ __forceinline__ DfRef df_ref(const Slot& s, int sel) {
   if (sel == SEL_L) return DfRef{dfm(s.L), s.Linv, s.n_pad, s.n_pad};
   if (sel == SEL_COV) return DfRef{dfm(s.Wk), s.Wd, s.nd_pad, s.n_pad};
+  if (sel == SEL_AUX) return DfRef{dfm(s.Qp), s.Linv, s.aux_n, s.n_pad};
   return DfRef{dfm(s.S), s.SLinv, s.k_pad, s.k_pad};
 }
 __device__ __forceinline__ double* vec_ref_df(const Slot& s, int v) {
@@ -218,7 +219,7 @@ __global__ void k_s_pad_identity(Slot* slots) {
 // the factor tile (double-float, upper part zeroed) and the inverse tile (double-float, in the
 // FP64-sized cells of the inverse-tile array).
 constexpr int DG_LD = TB + 1;
-constexpr int DG_THREADS = 512;
+constexpr int DG_THREADS = 1024;
 __device__ __forceinline__ df dg_ld(const float2* t, int i, int c) { return df_make(t[i * DG_LD + c].x, t[i * DG_LD + c].y); }
 __device__ __forceinline__ void dg_st(float2* t, int i, int c, df v) { t[i * DG_LD + c] = make_float2(v.hi, v.lo); }
 
@@ -701,4 +702,139 @@ __global__ void k_add_cct_df(Slot* slots) {
 void launch_add_cct_df(Slot* slots, int nslots, cudaStream_t st) {
   count_launch("k_add_cct_df"), k_add_cct_df<<<dim3(1024, nslots), 256, 0, st>>>(slots);
 }
+}  // namespace inla
+
+namespace inla {
+
+// ---- Moore-Penrose / Woodbury route (Section 3.1, Eq. (woodeqn)) ----
+
+// Q+ entry (i, j), internal indices: 0 across blocks; fixed 1 / prec and iid exp(-theta) on the
+// diagonal; the dense block's covariance (double-float distance and exp, as the prior build);
+// Kronecker blocks exp(-theta) times the product of the factors' pseudo-inverse entries (last
+// factor fastest); 0 on the padding.
+__device__ df pinv_prior_entry(const Slot& s, const ModelDev& md, int i, int j) {
+  if (i >= s.n || j >= s.n) return df_make(0.f, 0.f);
+  int bi = -1;
+  for (int b = 0; b < md.nblk; ++b)
+    if (i >= md.blk[b].off && i < md.blk[b].off + md.blk[b].size) bi = b;
+  const BlockInfo& B = md.blk[bi];
+  if (j < B.off || j >= B.off + B.size) return df_make(0.f, 0.f);
+  const int li = i - B.off, lj = j - B.off;
+  switch (B.kind) {
+    case INLA_BLOCK_FIXED:
+      return li == lj ? df_from_double(1.0 / B.prec) : df_make(0.f, 0.f);
+    case INLA_BLOCK_IID:
+      return li == lj ? df_from_double(exp(-s.theta[B.theta_idx])) : df_make(0.f, 0.f);
+    case INLA_BLOCK_DENSE_EXP: {
+      const double* P = md.points;
+      df v = cov_entry_df(df_from_double(P[2 * li]), df_from_double(P[2 * li + 1]), df_from_double(P[2 * lj]),
+                          df_from_double(P[2 * lj + 1]), df_from_double(exp(-s.theta[md.theta_rx])),
+                          df_from_double(exp(-s.theta[md.theta_ry])), df_from_double(exp(2.0 * s.theta[md.theta_sigma])));
+      if (li == lj) {
+        double diag_add = md.nugget;
+        if (md.theta_iid >= 0) diag_add += exp(-s.theta[md.theta_iid]);
+        v = df_add(v, df_from_double(diag_add));
+      }
+      return v;
+    }
+    default: {  // Kronecker
+      double prod = exp(-s.theta[B.theta_idx]);
+      int ri = li, rj = lj;
+      for (int f = B.nf - 1; f >= 0; --f) {
+        const int fs = B.fsize[f];
+        const int a = ri % fs, c = rj % fs;
+        ri /= fs;
+        rj /= fs;
+        prod *= md.factor_pinv[B.pinv_off[f] + (int64_t)a * fs + c];
+      }
+      return df_from_double(prod);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_woodbury_qplus_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const ModelDev& md = *s.md;
+  const int n = s.n_pad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    df_store(dfm(s.Wk) + e, pinv_prior_entry(s, md, i, j));
+  }
+}
+
+// G row r = sqrt(w_r) sum_{e in row r of A} a_e Q+[col_e, :] (rows r >= m zero), into L
+__global__ void __launch_bounds__(256) k_woodbury_g_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const ModelDev& md = *s.md;
+  const int n = s.n_pad;
+  for (int r = blockIdx.x; r < s.aux_n; r += gridDim.x) {
+    float2* G = dfm(s.L) + (size_t)r * n;
+    if (r >= s.m) {
+      for (int c = threadIdx.x; c < n; c += blockDim.x) G[c] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const double sw = sqrt(s.w[r]);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      df acc = df_make(0.f, 0.f);
+      for (int64_t e = md.A_rowptr[r]; e < md.A_rowptr[r + 1]; ++e)
+        acc = df_add(acc, df_mul(df_from_double(sw * md.A_val[e]), df_load(dfm(s.Wk) + (size_t)md.A_col[e] * n + c)));
+      df_store(G + c, acc);
+    }
+  }
+}
+
+// M = I + G B^T (lower triangle, aux_n x aux_n, identity on the padding), into Qp
+__global__ void __launch_bounds__(256) k_woodbury_m_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const ModelDev& md = *s.md;
+  const int n = s.n_pad, na = s.aux_n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)na * na; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / na), l = (int)(e % na);
+    if (l > i) continue;
+    df v = df_make(i == l ? 1.f : 0.f, 0.f);
+    if (i < s.m && l < s.m) {
+      const double sw = sqrt(s.w[l]);
+      const float2* G = dfm(s.L) + (size_t)i * n;
+      for (int64_t q = md.A_rowptr[l]; q < md.A_rowptr[l + 1]; ++q)
+        v = df_add(v, df_mul(df_from_double(sw * md.A_val[q]), df_load(G + md.A_col[q])));
+    }
+    df_store(dfm(s.Qp) + (size_t)i * n + l, v);
+  }
+}
+
+// t1[j] = Q+_jj - sum_{r < aux_n} Z[r][j]^2 with Z = L_M^-1 G held in L
+__global__ void __launch_bounds__(256) k_woodbury_var_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const int jt = blockIdx.x;
+  if (jt >= s.n_pad / TB) return;
+  __shared__ double part[4][TB];
+  const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  df acc = df_make(0.f, 0.f);
+  const float2* Z = dfm(s.L);
+  for (int r = g; r < s.aux_n; r += 4) {
+    const df z = df_load(Z + (size_t)r * s.n_pad + jt * TB + c);
+    acc = df_fma(acc, z, z);
+  }
+  part[g][c] = df_to_double(acc);
+  __syncthreads();
+  if (threadIdx.x < TB) {
+    const int j = jt * TB + threadIdx.x;
+    const double t2 = ((part[0][threadIdx.x] + part[1][threadIdx.x]) + part[2][threadIdx.x]) + part[3][threadIdx.x];
+    s.t1[j] = df_to_double(df_load(dfm(s.Wk) + (size_t)j * s.n_pad + j)) - t2;
+  }
+}
+
+void launch_woodbury_terms_df(Slot* slots, int nslots, int max_n, cudaStream_t st) {
+  count_launch("k_woodbury_qplus_df"), k_woodbury_qplus_df<<<dim3(4096, nslots), 256, 0, st>>>(slots);
+  count_launch("k_woodbury_g_df"), k_woodbury_g_df<<<dim3(std::min(max_n, 8192), nslots), 256, 0, st>>>(slots);
+  count_launch("k_woodbury_m_df"), k_woodbury_m_df<<<dim3(4096, nslots), 256, 0, st>>>(slots);
+}
+void launch_woodbury_var_df(Slot* slots, int nslots, int max_n, cudaStream_t st) {
+  count_launch("k_woodbury_var_df"), k_woodbury_var_df<<<dim3(max_n / TB, nslots), 256, 0, st>>>(slots);
+}
+
 }  // namespace inla

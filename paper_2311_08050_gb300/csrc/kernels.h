@@ -9,6 +9,7 @@ enum MatSel {
   SEL_L = 0,      // Q / its factor (n_pad), diagonal-tile inverses in Linv
   SEL_COV = 1,    // dense-block covariance / its factor in Wk (nd_pad), inverses in Wd
   SEL_S = 2,      // constraint Schur matrix S (k_pad), inverses in SLinv
+  SEL_AUX = 3,    // the Moore-Penrose route's m x m system (aux_n, held in Qp), inverses in Linv
 };
 // Destination of a triangular inverse.
 enum InvDst { DST_L = 0, DST_WK = 1 };

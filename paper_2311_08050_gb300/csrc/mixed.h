@@ -81,5 +81,10 @@ int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // Y = F^-T (upper)
 int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = Y Y^T (Y in L)
 int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S
 int mixed_var_constraint(Batch& B);                           // t2 = diag(Q^-1 C^T S^-1 C Q^-1)
+int mixed_woodbury_variances(Batch& B);                       // t1 = diag(Sigma*) of Eq. (woodeqn)
+// Moore-Penrose route kernels (k_df.cu): Q+ into Wk, G = D^1/2 A Q+ into L, M = I + G (D^1/2 A)^T
+// into Qp; then t1 = diag(Q+) - column sums of squares of the first aux_n rows of L
+void launch_woodbury_terms_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
+void launch_woodbury_var_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
 
 }  // namespace inla

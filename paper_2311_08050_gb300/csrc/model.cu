@@ -22,8 +22,13 @@
 
 namespace inla {
 
-// cyclic Jacobi eigenvalues of a small symmetric matrix (row-major, n x n)
-static std::vector<double> jacobi_eigenvalues(std::vector<double> a, int n) {
+// cyclic Jacobi eigenvalues of a small symmetric matrix (row-major, n x n); with vecs, also the
+// eigenvectors (columns of the accumulated rotations: a = V diag(ev) V^T)
+static std::vector<double> jacobi_eigenvalues(std::vector<double> a, int n, std::vector<double>* vecs = nullptr) {
+  if (vecs) {
+    vecs->assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) (*vecs)[(size_t)i * n + i] = 1.0;
+  }
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int i = 0; i < n; ++i)
@@ -50,6 +55,13 @@ static std::vector<double> jacobi_eigenvalues(std::vector<double> a, int n) {
           a[p * n + k] = c * apk - s * aqk;
           a[q * n + k] = s * apk + c * aqk;
         }
+        if (vecs)
+          for (int k = 0; k < n; ++k) {
+            double* V = vecs->data();
+            const double vkp = V[k * n + p], vkq = V[k * n + q];
+            V[k * n + p] = c * vkp - s * vkq;
+            V[k * n + q] = s * vkp + c * vkq;
+          }
       }
   }
   std::vector<double> ev(n);
@@ -326,6 +338,21 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
     if (D->blocks[crow_block[r]].kind != INLA_BLOCK_KRON) return INLA_E_UNSUPPORTED;
     constrained_block[crow_block[r]]++;
   }
+  // per block in internal order, for the Moore-Penrose route: kind, offset, size, and the
+  // factors' pseudo-inverses of the Kronecker blocks
+  if (D->nblocks > MAX_BLOCKS) return INLA_E_UNSUPPORTED;
+  std::vector<BlockInfo> binfo(D->nblocks);
+  std::vector<double> pinv;
+  for (int b = 0; b < D->nblocks; ++b) {
+    const inla_block& B = D->blocks[b];
+    BlockInfo& bi = binfo[b];
+    std::memset(&bi, 0, sizeof(bi));
+    bi.kind = B.kind;
+    bi.off = bstart_int[b];
+    bi.size = B.size;
+    bi.theta_idx = B.kind == INLA_BLOCK_FIXED ? -1 : B.theta_idx;
+    bi.prec = B.prec;
+  }
   for (int b = 0; b < D->nblocks; ++b) {
     const inla_block& B = D->blocks[b];
     const int s0 = bstart_int[b];
@@ -345,13 +372,28 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
       std::vector<std::vector<double>> ev(nf);
       for (int f = 0; f < nf; ++f) {
         INLA_TRY(factor_matrix(B.factors[f], R[f]));
-        ev[f] = jacobi_eigenvalues(R[f], B.factors[f].size);
+        std::vector<double> V;
+        const int fs = B.factors[f].size;
+        ev[f] = jacobi_eigenvalues(R[f], fs, &V);
         double mx = 0.0;
         for (double v : ev[f]) mx = std::max(mx, std::fabs(v));
         for (double& v : ev[f])
           if (std::fabs(v) <= 1e-9 * mx) v = 0.0;
           else if (v < 0) return INLA_E_BADARG;  // structure must be positive semi-definite
+        // Moore-Penrose pseudo-inverse of the factor: sum over the nonzero eigenvalues of
+        // v v^T / lambda (the pseudo-inverse of a Kronecker product is that of the factors)
+        BlockInfo& bi = binfo[b];
+        bi.pinv_off[f] = (int64_t)pinv.size();
+        bi.fsize[f] = fs;
+        for (int i = 0; i < fs; ++i)
+          for (int j = 0; j < fs; ++j) {
+            double a = 0.0;
+            for (int e = 0; e < fs; ++e)
+              if (ev[f][e] != 0.0) a += V[(size_t)i * fs + e] * V[(size_t)j * fs + e] / ev[f][e];
+            pinv.push_back(a);
+          }
       }
+      binfo[b].nf = nf;
       // sparse Kronecker product, lower triangle, every diagonal present
       int sz[3] = {1, 1, 1};
       for (int f = 0; f < nf; ++f) sz[f + (3 - nf)] = B.factors[f].size;
@@ -466,6 +508,9 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
   INLA_TRY(dev_copy(M, &d.pc_obs, pobs.data(), pobs.size()));
   INLA_TRY(dev_copy(M, &d.pc_coef, pcoef.data(), pcoef.size()));
   INLA_TRY(dev_copy(M, &d.heavy_cols, heavy_cols.data(), heavy_cols.size()));
+  d.nblk = D->nblocks;
+  for (int b = 0; b < D->nblocks; ++b) d.blk[b] = binfo[b];
+  INLA_TRY(dev_copy(M, &d.factor_pinv, pinv.data(), pinv.size()));
   INLA_TRY(dev_copy(M, &d.obs_ptr, optr.data(), optr.size()));
   INLA_TRY(dev_copy(M, &d.obs_pair, opair.data(), opair.size()));
   INLA_TRY(dev_copy(M, &d.obs_coef, ocoef.data(), ocoef.size()));

@@ -24,6 +24,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 OPT_DEVICE_OUT = 1
 OPT_NO_SHARED_START = 2
 OPT_VB_MEAN = 4
+OPT_WOODBURY_VAR = 8
 
 EXPORTED = ["inla_opts_default", "inla_model_create", "inla_model_destroy", "inla_eval_theta",
             "inla_eval_batch", "inla_marginals", "inla_status_string"]
