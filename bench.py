@@ -289,6 +289,8 @@ def run_ours(args):
     traffic = GEMM_TRAFFIC_RATIO * alg_bytes_per_launch if (GEMM_TRAFFIC_RATIO and alg_bytes_per_launch) else None
     n_pad = ((spec.n + 255) // 256) * 256
     outer_block = {f"slices{sl}": int(L.inla_test_outer_block(n_pad, sl)) for sl in (args.newton_slices, args.slices)}
+    outer_block["inverse"] = {f"slices{sl}": int(L.inla_test_inverse_block(n_pad, sl))
+                              for sl in sorted({args.prior_slices or args.slices, args.slices})}
     # achieved = the method's flops (2 x needed output elements x K per GEMM launch, i.e. the
     # Cholesky / inverse / product work itself) per second of GEMM time; the BF16 slice passes
     # the tensor pipe runs for them are reported separately

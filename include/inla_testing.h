@@ -77,9 +77,13 @@ int inla_test_newton_trace(double *steps, int32_t *refactored, int32_t cap);
  * factored with `slices` slices (tuned per batch size; this returns the choice for the largest
  * batch decided): 256 or 512 once its two timed candidate runs are complete, 0 while undecided
  * (sizes below 1024 always use 256).  With the environment variable
- * INLA_OUTER_BLOCK=256 or 512 (read once) every size uses that block, untuned (for profiler
- * captures, whose timings would mislead the tuner), and this returns it. */
+ * INLA_OUTER_BLOCK=256 or 512 (read once) every size and every tuned routine uses that block,
+ * untuned (for profiler captures, whose timings would mislead the tuner), and this returns it. */
 int inla_test_outer_block(int32_t n_pad, int32_t slices);
+
+/* The same for the mixed transposed inverse of a factor (Y = F^-T: the inverse of the prior
+ * covariance's factor and, for the marginal variances, of the factor at the mode). */
+int inla_test_inverse_block(int32_t n_pad, int32_t slices);
 
 /* One cooperative double-float triangular solve of the mixed path on a caller-given lower
  * factor L (host, row-major n x n FP64, n a multiple of 64): x = L^-1 b (backward = 0) or

@@ -1062,4 +1062,5 @@ extern "C" int inla_test_newton_trace(double* steps, int32_t* refactored, int32_
 }
 
 extern "C" int inla_test_outer_block(int32_t n_pad, int32_t slices) { return mixed_nb_choice(n_pad, slices); }
+extern "C" int inla_test_inverse_block(int32_t n_pad, int32_t slices) { return mixed_inverse_nb_choice(n_pad, slices); }
 

@@ -14,7 +14,6 @@ namespace inla {
 
 namespace {
 
-constexpr int NB = MIXED_NB;   // outer block of the triangular solves
 constexpr int IB = TB;    // inner block (64)
 
 struct MRef {
@@ -155,9 +154,11 @@ void mixed_graphs_clear() {
   g_potrf_graphs.clear();
 }
 
-// Outer-block tuner: for each (matrix size, slices) the first factorisation runs with each
-// candidate in turn, timed with CUDA events on the stream (the factorisations are the real ones:
-// no extra work); once both timings are complete, the faster candidate is used from then on.
+// Outer-block tuner: for each blocked routine (the Cholesky, the transposed inverse, the forward
+// substitution with many right-hand sides) and shape (matrix size, slices, slots, right-hand
+// sides), the first two real calls run with the candidates 256 and 512 in turn, timed with CUDA
+// events on the stream (no extra work); once both timings are complete, the faster candidate is
+// used from then on.
 namespace {
 constexpr int kNbCandidates[2] = {256, 512};
 struct NbTune {
@@ -165,10 +166,11 @@ struct NbTune {
   int runs = 0;
   int best = 0;  // 0: undecided
 };
-std::map<std::tuple<int, int, int>, NbTune> g_nb_tune;  // (matrix size, slices, slots)
+enum { NB_POTRF = 0, NB_INVERSE = 1, NB_TRSM = 2 };
+std::map<std::tuple<int, int, int, int, int>, NbTune> g_nb_tune;  // (routine, size, slices, slots, rhs)
 
-// INLA_OUTER_BLOCK=256 or 512 pins the outer block of every mixed Cholesky (no tuning runs):
-// under a profiler the tuner's timings would not reflect the unprofiled program.
+// INLA_OUTER_BLOCK=256 or 512 pins the outer block of every tuned mixed routine (no tuning
+// runs): under a profiler the tuner's timings would not reflect the unprofiled program.
 int pinned_nb() {
   static const int v = [] {
     const char* e = getenv("INLA_OUTER_BLOCK");
@@ -178,12 +180,12 @@ int pinned_nb() {
   return v;
 }
 
-int pick_nb(const MRef& M, int S, int nslots, NbTune*& tune, int& cand) {
+int pick_nb(int routine, int n, int S, int nslots, int rhs, NbTune*& tune, int& cand) {
   tune = nullptr;
   cand = -1;
   if (pinned_nb()) return pinned_nb();
-  if (M.n < 2 * kNbCandidates[1]) return kNbCandidates[0];  // too small for the wider panel to matter
-  NbTune& t = g_nb_tune[std::make_tuple(M.n, S, nslots)];
+  if (n < 2 * kNbCandidates[1]) return kNbCandidates[0];  // too small for the wider block to matter
+  NbTune& t = g_nb_tune[std::make_tuple(routine, n, S, nslots, rhs)];
   if (t.best) return t.best;
   if (t.runs == 2) {
     float ms[2] = {0.f, 0.f};
@@ -204,33 +206,53 @@ int pick_nb(const MRef& M, int S, int nslots, NbTune*& tune, int& cand) {
   tune = &t;
   return kNbCandidates[cand];
 }
-}  // namespace
 
-int mixed_nb_choice(int n, int S) {
+// A tuning run brackets the routine's launches with the candidate's events.
+struct TuneTimer {
+  NbTune* t;
+  int cand;
+  cudaStream_t st;
+  int begin() {
+    if (!t) return INLA_OK;
+    for (auto& e : t->ev[cand])
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return INLA_E_CUDA;
+    cudaEventRecord(t->ev[cand][0], st);
+    return INLA_OK;
+  }
+  void end() {
+    if (!t) return;
+    cudaEventRecord(t->ev[cand][1], st);
+    ++t->runs;
+  }
+};
+
+int nb_choice(int routine, int n, int S) {
   if (pinned_nb()) return pinned_nb();
   int best = 0, most_slots = -1;  // the decided choice for the largest batch of this size
   for (const auto& kv : g_nb_tune)
-    if (std::get<0>(kv.first) == n && std::get<1>(kv.first) == S && kv.second.best &&
-        std::get<2>(kv.first) > most_slots) {
-      most_slots = std::get<2>(kv.first);
+    if (std::get<0>(kv.first) == routine && std::get<1>(kv.first) == n && std::get<2>(kv.first) == S &&
+        kv.second.best && std::get<3>(kv.first) > most_slots) {
+      most_slots = std::get<3>(kv.first);
       best = kv.second.best;
     }
   return best;
 }
+}  // namespace
+
+int mixed_nb_choice(int n, int S) { return nb_choice(NB_POTRF, n, S); }
+int mixed_inverse_nb_choice(int n, int S) { return nb_choice(NB_INVERSE, n, S); }
 
 int mixed_potrf(Batch& B, int sel) {
   const MRef M = mref(B, sel);
   NbTune* tune = nullptr;
   int cand = -1;
-  const int nb = pick_nb(M, B.S, B.n, tune, cand);
+  const int nb = pick_nb(NB_POTRF, M.n, B.S, B.n, 0, tune, cand);
   if (tune) {
     // a tuning run: timed, never captured
-    for (auto& e : tune->ev[cand])
-      if (!e && cudaEventCreate(&e) != cudaSuccess) return INLA_E_CUDA;
-    cudaEventRecord(tune->ev[cand][0], B.st);
+    TuneTimer tt{tune, cand, B.st};
+    INLA_TRY(tt.begin());
     const int rc = mixed_potrf_launches(B, sel, nb);
-    cudaEventRecord(tune->ev[cand][1], B.st);
-    ++tune->runs;
+    tt.end();
     return rc;
   }
   if (B.st == nullptr || prof_active() || oz_stats_active() || debug_sync_enabled())
@@ -276,8 +298,8 @@ int mixed_potrf(Batch& B, int sel) {
 // X <- F^-1 X (forward substitution, F lower-triangular factor selected by `fsel`), X with
 // `nrows` = F.n rows and `ncols` columns (leading dimension ldx).  identity: X = I on entry,
 // so block row K only has nonzero columns [0, end of block K).
-static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, int ncols, bool identity) {
-  const MRef F = mref(B, fsel);
+static int trsm_left_nb(Batch& B, const MRef& F, float2* X, int64_t x_stride, int ldx, int ncols, bool identity,
+                        int NB) {
   const int n = F.n, S = B.S;
   for (int K0 = 0; K0 < n; K0 += NB) {
     const int kend = std::min(K0 + NB, n);
@@ -286,8 +308,8 @@ static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, i
       // X[j0 tile, 0:nc] = Linv_j X[j0 tile, 0:nc]
       OzOperand pl = operand(B.PA, B.EA, IB, IB);
       OzOperand px = operand(B.PB, B.EB, nc, IB);
-      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB,
-                  false, pl, S, B.n, B.st);
+      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
+                  IB, false, pl, S, B.n, B.st);
       oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px, S, B.n, B.st);
       OzArgs a = gemm_args(B, X + (int64_t)j0 * ldx, x_stride, ldx, IB, nc, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(pl, px, a, B.n, B.st));
@@ -314,14 +336,24 @@ static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, i
   }
   return INLA_OK;
 }
+static int trsm_left(Batch& B, int fsel, float2* X, int64_t x_stride, int ldx, int ncols, bool identity) {
+  const MRef F = mref(B, fsel);
+  NbTune* tune = nullptr;
+  int cand = -1;
+  const int nb = pick_nb(NB_TRSM, F.n, B.S, B.n, ncols, tune, cand);
+  TuneTimer tt{tune, cand, B.st};
+  INLA_TRY(tt.begin());
+  const int rc = trsm_left_nb(B, F, X, x_stride, ldx, ncols, identity, nb);
+  if (rc == INLA_OK) tt.end();
+  return rc;
+}
 
 // Y = F^-T (upper triangular: the transpose of the inverse of the lower factor F), written into
 // Wk (into_wk) or into L.  Column blocks of Y in increasing order: Y[:, K] = Y[:, K] Linv_K^T, then
 // Y[:, J] -= Y[:, K] F[J, K]^T for the blocks J > K -- the transpose of forward substitution on
 // the rows of F^-1, so that every operand is sliced by rows (Y's column block and F's row block
 // are both K-contiguous) and only the first kend rows of Y (its nonzero part) enter.
-int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
-  const MRef F = mref(B, sel);
+static int inverse_factor_nb(Batch& B, const MRef& F, bool into_wk, int NB) {
   const Slot& s0 = B.h[0];
   const int n = F.n, S = B.S;
   float2* Y = reinterpret_cast<float2*>(into_wk ? s0.Wk : s0.L);
@@ -337,9 +369,9 @@ int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
       // Y[0:nc, j0 tile] = Y[0:nc, j0 tile] Linv_j^T
       OzOperand py = operand(B.PA, B.EA, nc, IB);
       OzOperand pl = operand(B.PB, B.EB, IB, IB);
+      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
+                  IB, false, pl, S, B.n, B.st);
       oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py, S, B.n, B.st);
-      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB, IB,
-                  false, pl, S, B.n, B.st);
       OzArgs a = gemm_args(B, Y + j0, ys, ld, nc, IB, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(py, pl, a, B.n, B.st));
       if (j0 + IB < kend) {
@@ -347,8 +379,8 @@ int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
         const int R = kend - j0 - IB;
         OzOperand py2 = operand(B.PA, B.EA, nc, IB);
         OzOperand pf = operand(B.PB, B.EB, R, IB);
-        oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py2, S, B.n, B.st);
         oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, B.st);
+        oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py2, S, B.n, B.st);
         OzArgs u = gemm_args(B, Y + j0 + IB, ys, ld, nc, R, IB, 1.f, -1.f);
         INLA_TRY(oz_gemm(py2, pf, u, B.n, B.st));
       }
@@ -358,13 +390,24 @@ int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
       // Y[0:nc, kend .. n] -= Y[0:nc, K0:kend] F[kend .. n, K0:kend]^T
       OzOperand py = operand(B.PA, B.EA, nc, kend - K0);
       OzOperand pf = operand(B.PB, B.EB, R, kend - K0);
-      oz_slice_df(Y, ys, ld, 0, K0, nc, kend - K0, false, py, S, B.n, B.st);
       oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, B.st);
+      oz_slice_df(Y, ys, ld, 0, K0, nc, kend - K0, false, py, S, B.n, B.st);
       OzArgs u = gemm_args(B, Y + kend, ys, ld, nc, R, kend - K0, 1.f, -1.f);
       INLA_TRY(oz_gemm(py, pf, u, B.n, B.st));
     }
   }
   return INLA_OK;
+}
+int mixed_inverse_factor(Batch& B, int sel, bool into_wk) {
+  const MRef F = mref(B, sel);
+  NbTune* tune = nullptr;
+  int cand = -1;
+  const int nb = pick_nb(NB_INVERSE, F.n, B.S, B.n, 0, tune, cand);
+  TuneTimer tt{tune, cand, B.st};
+  INLA_TRY(tt.begin());
+  const int rc = inverse_factor_nb(B, F, into_wk, nb);
+  if (rc == INLA_OK) tt.end();
+  return rc;
 }
 
 // Q_p[0:nd, 0:nd] = W^T W = Y Y^T with Y = L_Sigma^-T held in L (upper): row k of Y is nonzero

@@ -441,6 +441,19 @@ __global__ void __launch_bounds__(256) k_trsv_df(TrsvArgs p) {
     double* dst = vec_ref_df(s, p.dst);
     int32_t* flg = p.flags + (size_t)sl * p.T;
     const float2* Li = reinterpret_cast<const float2*>(M.Linv) + (size_t)i * TB * TB;
+    // the diagonal-tile inverse and this tile of src, read now: off the chain of ready flags
+    float2 liv[16];
+    if (!p.backward) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        liv[2 * r] = Li[(warp * 8 + r) * TB + lane];
+        liv[2 * r + 1] = Li[(warp * 8 + r) * TB + lane + 32];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) liv[r] = Li[(g * 16 + r) * TB + c];
+    }
+    const double srcv = tid < TB ? src[(size_t)i * TB + tid] : 0.0;
     df acc[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r] = df_make(0.f, 0.f);
@@ -513,7 +526,7 @@ __global__ void __launch_bounds__(256) k_trsv_df(TrsvArgs p) {
       df sum = df_make(part[0][tid].x, part[0][tid].y);
       if (p.backward)
         for (int q = 1; q < 4; ++q) sum = df_add_fast(sum, df_make(part[q][tid].x, part[q][tid].y));
-      const df a = df_add_fast(df_from_double(src[(size_t)i * TB + tid]), df_neg(sum));
+      const df a = df_add_fast(df_from_double(srcv), df_neg(sum));
       av[tid] = make_float2(a.hi, a.lo);
     }
     __syncthreads();
@@ -523,8 +536,8 @@ __global__ void __launch_bounds__(256) k_trsv_df(TrsvArgs p) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int row = warp * 8 + r;
-        df v = df_mul(df_make(Li[row * TB + lane].x, Li[row * TB + lane].y), a0);
-        v = df_add_fast(v, df_mul(df_make(Li[row * TB + lane + 32].x, Li[row * TB + lane + 32].y), a1));
+        df v = df_mul(df_make(liv[2 * r].x, liv[2 * r].y), a0);
+        v = df_add_fast(v, df_mul(df_make(liv[2 * r + 1].x, liv[2 * r + 1].y), a1));
         v = df_shfl_xor_sum(v);
         if (lane == 0) dst[(size_t)i * TB + row] = df_to_double(v);
       }
@@ -532,8 +545,7 @@ __global__ void __launch_bounds__(256) k_trsv_df(TrsvArgs p) {
       df v = df_make(0.f, 0.f);
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const float2 l = Li[(g * 16 + r) * TB + c];
-        v = df_add_fast(v, df_mul(df_make(l.x, l.y), df_make(av[g * 16 + r].x, av[g * 16 + r].y)));
+        v = df_add_fast(v, df_mul(df_make(liv[r].x, liv[r].y), df_make(av[g * 16 + r].x, av[g * 16 + r].y)));
       }
       part[g][c] = make_float2(v.hi, v.lo);
       __syncthreads();

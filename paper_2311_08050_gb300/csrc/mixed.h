@@ -37,9 +37,8 @@ void launch_diag_ones_df(float2* base, int64_t slot_stride, int ld, int n, int n
 // Outer block of the mixed blocked routines: the trailing updates have K = outer block (C is
 // read and written n^3 / (3 NB) times per factorisation).  512 (one exact 512-wide chunk per
 // update) halves that traffic but deepens the recursive panel factorisation inside each outer
-// panel; the Cholesky picks between the candidates per matrix size (mixed_potrf's tuner), the
-// triangular solves use MIXED_NB.
-constexpr int MIXED_NB = 256;
+// panel (Cholesky) or doubles the 64-wide steps inside each outer block (triangular routines);
+// each routine picks between 256 and 512 per shape (eval_mixed.cu's tuner).
 constexpr int MIXED_NB_MAX = 512;   // workspace capacity (largest candidate)
 
 // A batch of slots with identical shapes (uniform per-slot strides).
@@ -76,7 +75,8 @@ int launch_vb_terms(Slot* slots, int nslots, int max_m, cudaStream_t st);
 // mixed blocked routines (eval_mixed.cu)
 int mixed_potrf(Batch& B, int sel);          // replays a captured CUDA graph for a known layout
 void mixed_graphs_clear();                   // drop every captured graph (workspace reallocated)
-int mixed_nb_choice(int n, int S);           // the tuned outer block for (n, S), 0 if undecided
+int mixed_nb_choice(int n, int S);           // the Cholesky's tuned outer block for (n, S), 0 if undecided
+int mixed_inverse_nb_choice(int n, int S);   // the transposed inverse's, likewise
 int mixed_inverse_factor(Batch& B, int sel, bool into_wk);   // Y = F^-T (upper), F by sel
 int mixed_lauum_cov(Batch& B);                                // Q_p[0:nd,0:nd] = Y Y^T (Y in L)
 int mixed_schur(Batch& B);                                    // Z = L^-1 C^T, S = Z^T Z, factor S

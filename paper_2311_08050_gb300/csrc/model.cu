@@ -268,17 +268,34 @@ static int create_impl(const inla_model_desc* D, inla_model* M) {
     int32_t obs;
     double coef;
   };
+  // the contributions ordered by (row, column) of the pair, observations ascending within a pair:
+  // a counting sort by the row (observations are visited in order, so each row's bucket is
+  // already ordered by observation), then a stable sort by column inside the buckets that need it
   std::vector<Contrib> con;
-  for (int i = 0; i < m; ++i)
-    for (int64_t a = Arp[i]; a < Arp[i + 1]; ++a)
-      for (int64_t b = Arp[i]; b < Arp[i + 1]; ++b) {
-        const int ca = Acol[a], cb = Acol[b];
-        if (ca < cb || (ca == cb && a != b)) continue;
-        con.push_back(Contrib{(int64_t)ca * n_pad + cb, i, Aval[a] * Aval[b]});
-      }
-  std::sort(con.begin(), con.end(), [](const Contrib& x, const Contrib& y) {
-    return x.key != y.key ? x.key < y.key : x.obs < y.obs;
-  });
+  {
+    auto for_each_pair = [&](auto&& f) {
+      for (int i = 0; i < m; ++i)
+        for (int64_t a = Arp[i]; a < Arp[i + 1]; ++a)
+          for (int64_t b = Arp[i]; b < Arp[i + 1]; ++b) {
+            const int ca = Acol[a], cb = Acol[b];
+            if (ca < cb || (ca == cb && a != b)) continue;
+            f(i, ca, cb, Aval[a] * Aval[b]);
+          }
+    };
+    std::vector<int64_t> start((size_t)n_pad + 1, 0);
+    for_each_pair([&](int, int ca, int, double) { ++start[(size_t)ca + 1]; });
+    for (int j = 0; j < n_pad; ++j) start[j + 1] += start[j];
+    con.resize((size_t)start[n_pad]);
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for_each_pair([&](int i, int ca, int cb, double v) {
+      con[(size_t)fill[ca]++] = Contrib{(int64_t)ca * n_pad + cb, i, v};
+    });
+    for (int j = 0; j < n_pad; ++j) {
+      auto lo = con.begin() + start[j], hi = con.begin() + start[j + 1];
+      if (!std::is_sorted(lo, hi, [](const Contrib& x, const Contrib& y) { return x.key < y.key; }))
+        std::stable_sort(lo, hi, [](const Contrib& x, const Contrib& y) { return x.key < y.key; });
+    }
+  }
   std::vector<int32_t> prow, pcol, pobs;
   std::vector<int64_t> pptr;
   std::vector<double> pcoef;

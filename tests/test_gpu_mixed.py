@@ -221,8 +221,9 @@ def test_mixed_64_uneven_models_against_fp64_path():
 
 def test_outer_block_tuner_decides_and_results_agree():
     """The mixed Cholesky times its two outer-block candidates (256, 512) on the first two real
-    factorisations of a size and keeps the faster; every result along the way (both candidates
-    and the tuned choice) stays within the mixed tolerances of the oracle."""
+    factorisations of a size and keeps the faster, and so does the transposed inverse; every
+    result along the way (both candidates and the tuned choice) stays within the mixed
+    tolerances of the oracle."""
     import ctypes as C
     L = inla.lib()
     spec = synth.spatial_poisson("tune_n1500", synth.SEED_BASE + 71, 1499, 4000, [0.0, np.log(0.2)])
@@ -235,6 +236,8 @@ def test_outer_block_tuner_decides_and_results_agree():
     n_pad = 1536
     assert L.inla_test_outer_block(n_pad, 4) in (256, 512)
     assert L.inla_test_outer_block(n_pad, 5) in (256, 512)
+    # the transposed inverse (prior covariance, then the variances) is tuned the same way
+    assert L.inla_test_inverse_block(n_pad, 5) in (256, 512)
 
 
 
