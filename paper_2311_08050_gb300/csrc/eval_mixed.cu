@@ -6,6 +6,7 @@
 // tile columns; 64-wide inner steps in the triangular solves.
 #include <cstdlib>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include "df64.cuh"
 #include "mixed.h"
@@ -63,6 +64,61 @@ OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, in
   return a;
 }
 
+// Side stream: of two independent slicing launches (the operands of one GEMM), the first runs on
+// a per-device side stream forked from the batch's stream and joined back before the GEMM (events;
+// inside a graph capture they become graph edges), so that the two overlap.  Off (everything on
+// the batch's stream) for the legacy default stream and while the per-kernel profiler, the GEMM
+// statistics or debug synchronisation is on.
+struct SideRes {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideRes g_side[64];
+std::mutex g_side_mu;
+
+class Side {
+ public:
+  explicit Side(const Batch& B) : main_(B.st) {
+    if (!main_ || prof_active() || oz_stats_active() || debug_sync_enabled()) return;
+    const int dev = current_device();
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    SideRes& r = g_side[dev];
+    if (!r.st) {
+      SideRes n;
+      if (cudaStreamCreateWithFlags(&n.st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return;  // stays off (a partial set-up is leaked rather than half used)
+      }
+      r = n;
+    }
+    res_ = &r;
+  }
+  ~Side() { join(); }
+  // the stream for the side launch (ordered after everything issued so far on the batch's stream)
+  cudaStream_t fork() {
+    if (!res_) return main_;
+    cudaEventRecord(res_->fork, main_);
+    cudaStreamWaitEvent(res_->st, res_->fork, 0);
+    forked_ = true;
+    return res_->st;
+  }
+  // the batch's stream waits for the side launch (also on every early return, by the destructor)
+  void join() {
+    if (!forked_) return;
+    cudaEventRecord(res_->join, res_->st);
+    cudaStreamWaitEvent(main_, res_->join, 0);
+    forked_ = false;
+  }
+
+ private:
+  cudaStream_t main_;
+  SideRes* res_ = nullptr;
+  bool forked_ = false;
+};
+
 }  // namespace
 
 // Columns [c0, c1) of an outer panel, every slot: rows >= c0 hold A minus the updates of the
@@ -74,15 +130,18 @@ OzArgs gemm_args(const Batch& B, float2* C, int64_t c_stride, int ldc, int M, in
 static int mixed_panel(Batch& B, const MRef& M, int c0, int c1) {
   const int n = M.n, S = B.S;
   if (c1 - c0 <= IB) {
-    launch_potrf_diag_df(B.d_slots, B.n, M.sel, c0 / IB, B.st);
     const int R = n - c0 - IB;
+    // the panel below the tile is sliced (side stream) while the tile is factored
+    Side side(B);
+    OzOperand pa = operand(B.PA, B.EA, R > 0 ? R : 1, IB);
+    if (R > 0) oz_slice_df(M.base, M.stride, M.ld, c0 + IB, c0, R, IB, false, pa, S, B.n, side.fork());
+    launch_potrf_diag_df(B.d_slots, B.n, M.sel, c0 / IB, B.st);
     if (R <= 0) return INLA_OK;
     float2* panel = M.base + (int64_t)(c0 + IB) * M.ld + c0;
-    OzOperand pa = operand(B.PA, B.EA, R, IB);
     OzOperand pb = operand(B.PB, B.EB, IB, IB);
-    oz_slice_df(M.base, M.stride, M.ld, c0 + IB, c0, R, IB, false, pa, S, B.n, B.st);
     oz_slice_df(reinterpret_cast<float2*>(M.linv) + (int64_t)(c0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB,
                 false, pb, S, B.n, B.st);
+    side.join();
     OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
     return oz_gemm(pa, pb, a, B.n, B.st);
   }
@@ -308,9 +367,12 @@ static int trsm_left_nb(Batch& B, const MRef& F, float2* X, int64_t x_stride, in
       // X[j0 tile, 0:nc] = Linv_j X[j0 tile, 0:nc]
       OzOperand pl = operand(B.PA, B.EA, IB, IB);
       OzOperand px = operand(B.PB, B.EB, nc, IB);
-      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
-                  IB, false, pl, S, B.n, B.st);
-      oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px, S, B.n, B.st);
+      {
+        Side side(B);
+        oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
+                    IB, false, pl, S, B.n, side.fork());
+        oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px, S, B.n, B.st);
+      }
       OzArgs a = gemm_args(B, X + (int64_t)j0 * ldx, x_stride, ldx, IB, nc, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(pl, px, a, B.n, B.st));
       const int r_hi = kend;
@@ -318,8 +380,11 @@ static int trsm_left_nb(Batch& B, const MRef& F, float2* X, int64_t x_stride, in
         const int R = r_hi - j0 - IB;
         OzOperand pf = operand(B.PA, B.EA, R, IB);
         OzOperand px2 = operand(B.PB, B.EB, nc, IB);
-        oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, B.st);
-        oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px2, S, B.n, B.st);
+        {
+          Side side(B);
+          oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, side.fork());
+          oz_slice_df(X, x_stride, ldx, j0, 0, nc, IB, true, px2, S, B.n, B.st);
+        }
         OzArgs u = gemm_args(B, X + (int64_t)(j0 + IB) * ldx, x_stride, ldx, R, nc, IB, 1.f, -1.f);
         INLA_TRY(oz_gemm(pf, px2, u, B.n, B.st));
       }
@@ -328,8 +393,11 @@ static int trsm_left_nb(Batch& B, const MRef& F, float2* X, int64_t x_stride, in
     if (R > 0) {
       OzOperand pf = operand(B.PA, B.EA, R, kend - K0);
       OzOperand px = operand(B.PB, B.EB, nc, kend - K0);
-      oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, B.st);
-      oz_slice_df(X, x_stride, ldx, K0, 0, nc, kend - K0, true, px, S, B.n, B.st);
+      {
+        Side side(B);
+        oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, side.fork());
+        oz_slice_df(X, x_stride, ldx, K0, 0, nc, kend - K0, true, px, S, B.n, B.st);
+      }
       OzArgs u = gemm_args(B, X + (int64_t)kend * ldx, x_stride, ldx, R, nc, kend - K0, 1.f, -1.f);
       INLA_TRY(oz_gemm(pf, px, u, B.n, B.st));
     }
@@ -369,9 +437,12 @@ static int inverse_factor_nb(Batch& B, const MRef& F, bool into_wk, int NB) {
       // Y[0:nc, j0 tile] = Y[0:nc, j0 tile] Linv_j^T
       OzOperand py = operand(B.PA, B.EA, nc, IB);
       OzOperand pl = operand(B.PB, B.EB, IB, IB);
-      oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
-                  IB, false, pl, S, B.n, B.st);
-      oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py, S, B.n, B.st);
+      {
+        Side side(B);
+        oz_slice_df(reinterpret_cast<float2*>(F.linv) + (int64_t)(j0 / IB) * IB * IB, F.linv_stride, IB, 0, 0, IB,
+                    IB, false, pl, S, B.n, side.fork());
+        oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py, S, B.n, B.st);
+      }
       OzArgs a = gemm_args(B, Y + j0, ys, ld, nc, IB, IB, 0.f, 1.f);
       INLA_TRY(oz_gemm(py, pl, a, B.n, B.st));
       if (j0 + IB < kend) {
@@ -379,8 +450,11 @@ static int inverse_factor_nb(Batch& B, const MRef& F, bool into_wk, int NB) {
         const int R = kend - j0 - IB;
         OzOperand py2 = operand(B.PA, B.EA, nc, IB);
         OzOperand pf = operand(B.PB, B.EB, R, IB);
-        oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, B.st);
-        oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py2, S, B.n, B.st);
+        {
+          Side side(B);
+          oz_slice_df(F.base, F.stride, F.ld, j0 + IB, j0, R, IB, false, pf, S, B.n, side.fork());
+          oz_slice_df(Y, ys, ld, 0, j0, nc, IB, false, py2, S, B.n, B.st);
+        }
         OzArgs u = gemm_args(B, Y + j0 + IB, ys, ld, nc, R, IB, 1.f, -1.f);
         INLA_TRY(oz_gemm(py2, pf, u, B.n, B.st));
       }
@@ -390,8 +464,11 @@ static int inverse_factor_nb(Batch& B, const MRef& F, bool into_wk, int NB) {
       // Y[0:nc, kend .. n] -= Y[0:nc, K0:kend] F[kend .. n, K0:kend]^T
       OzOperand py = operand(B.PA, B.EA, nc, kend - K0);
       OzOperand pf = operand(B.PB, B.EB, R, kend - K0);
-      oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, B.st);
-      oz_slice_df(Y, ys, ld, 0, K0, nc, kend - K0, false, py, S, B.n, B.st);
+      {
+        Side side(B);
+        oz_slice_df(F.base, F.stride, F.ld, kend, K0, R, kend - K0, false, pf, S, B.n, side.fork());
+        oz_slice_df(Y, ys, ld, 0, K0, nc, kend - K0, false, py, S, B.n, B.st);
+      }
       OzArgs u = gemm_args(B, Y + kend, ys, ld, nc, R, kend - K0, 1.f, -1.f);
       INLA_TRY(oz_gemm(py, pf, u, B.n, B.st));
     }
