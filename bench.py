@@ -205,7 +205,7 @@ def run_ours(args):
     vp = [vbuf[b].data_ptr() for b in range(nb)]
     kw = dict(precision=args.precision, slices=args.slices, newton_slices=args.newton_slices, stream=sptr,
               device_out=True, x_out=xp, var_out=vp, prior_slices=args.prior_slices, reuse_below=args.reuse_below,
-              reuse_shrink=args.reuse_shrink)
+              reuse_shrink=args.reuse_shrink, var_slices=args.var_slices)
 
     def step():
         lp, st, _, _ = inla.eval_batch([model], thetas, **kw)
@@ -224,7 +224,9 @@ def run_ours(args):
         tr = tune.tune_precision(model, thetas[0], stream=sptr)
         kw.update(tr.opts())
         args.slices, args.newton_slices, args.prior_slices = tr.slices, tr.newton_slices, tr.prior_slices
+        args.var_slices = tr.var_slices
         tuned = {"prior_slices": tr.prior_slices, "slices": tr.slices, "newton_slices": tr.newton_slices,
+                 "var_slices": tr.var_slices,
                  "errors_vs_six_slices": tr.errors, "tuning_seconds": round(tr.seconds, 2),
                  "tried": [t["setting"] for t in tr.tried]}
     for _ in range(max(1, args.warmup)):
@@ -256,6 +258,12 @@ def run_ours(args):
     L.inla_test_profile_enable(0)
     stats = (C.c_double * 5)()
     L.inla_test_stats_read(stats)
+    # the instrumented step's Newton iterations (leading points, then followers): the largest step
+    # over the points still iterating and whether the factor was computed afresh
+    tr_steps, tr_ref = (C.c_double * 64)(), (C.c_int32 * 64)()
+    L.inla_test_newton_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
+    n_tr = min(64, int(L.inla_test_newton_trace(tr_steps, tr_ref, 64)))
+    newton_trace = [{"step": float("%.3g" % tr_steps[i]), "refactored": int(tr_ref[i])} for i in range(n_tr)]
     pbuf = C.create_string_buffer(1 << 18)
     L.inla_test_profile_read_by_phase(pbuf, 1 << 18)
     phbuf = C.create_string_buffer(1 << 12)
@@ -290,7 +298,7 @@ def run_ours(args):
     n_pad = ((spec.n + 255) // 256) * 256
     outer_block = {f"slices{sl}": int(L.inla_test_outer_block(n_pad, sl)) for sl in (args.newton_slices, args.slices)}
     outer_block["inverse"] = {f"slices{sl}": int(L.inla_test_inverse_block(n_pad, sl))
-                              for sl in sorted({args.prior_slices or args.slices, args.slices})}
+                              for sl in sorted({args.prior_slices or args.slices, args.var_slices or args.slices})}
     # achieved = the method's flops (2 x needed output elements x K per GEMM launch, i.e. the
     # Cholesky / inverse / product work itself) per second of GEMM time; the BF16 slice passes
     # the tensor pipe runs for them are reported separately
@@ -319,19 +327,21 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": f"bf16 Ozaki slices x{args.prior_slices or args.slices} (prior) / x{args.slices} (final factor) / "
-                    f"x{args.newton_slices} (Newton), "
+                    f"x{args.var_slices or args.slices} (its inverse: variances) / x{args.newton_slices} (Newton), "
                     "exact fp32 accumulation + df64 storage and diagonal tiles"
            if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; stands in for the paper's Poisson spatial workloads)",
            "config": {"workload": args.workload, "n": n, "m": spec.m, "theta_dim": spec.theta_dim, "batch": nb,
                       "precision": args.precision, "slices": args.slices, "newton_slices": args.newton_slices,
                       "prior_slices": args.prior_slices or args.slices,
+                      "var_slices": args.var_slices or args.slices,
                       "reuse_below": args.reuse_below or 1e-2, "reuse_shrink": args.reuse_shrink or 0.25,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "outer_block_tuned": outer_block, "precision_tuned": tuned,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},
            "clocks": clk.summary(), "roofline": roofline, "gpu_launches": None,
-           "kernel_breakdown": breakdown[:12], "phase_breakdown": phases, "phase_kernels": phase_kernels}
+           "kernel_breakdown": breakdown[:12], "phase_breakdown": phases, "phase_kernels": phase_kernels,
+           "newton_trace": newton_trace}
     # ---------------- end to end from host buffers ----------------
     if not args.no_e2e:
         # the step's inputs (observations, design, points, theta batch) in pinned host memory;
@@ -343,7 +353,8 @@ def run_ours(args):
             m2 = inla.Model(pspec)
             lp2, st2, xs2, vs2 = inla.eval_batch([m2], pthetas, precision=args.precision, slices=args.slices,
                                                  newton_slices=args.newton_slices, prior_slices=args.prior_slices,
-                                                 reuse_below=args.reuse_below, reuse_shrink=args.reuse_shrink)
+                                                 reuse_below=args.reuse_below, reuse_shrink=args.reuse_shrink,
+                                                 var_slices=args.var_slices)
             m2.close()
         t_e2e = time.perf_counter() - t0
         out["e2e"] = {"value": nb * e2e_steps / t_e2e * world, "unit": UNIT,
@@ -576,6 +587,8 @@ def main():
                     help="use the given slice counts instead of the autotuned rungs")
     ap.add_argument("--newton-slices", type=int, default=4, help="slices of the Newton-step factorisations")
     ap.add_argument("--prior-slices", type=int, default=0, help="slices of the prior inversion (0: --slices)")
+    ap.add_argument("--var-slices", type=int, default=0,
+                    help="slices of the inverse of the factor at the mode, for the variances (0: --slices)")
     ap.add_argument("--reuse-below", type=float, default=0.0, help="modified Newton: reuse a factor once steps are "
                     "below this (0: library default)")
     ap.add_argument("--reuse-shrink", type=float, default=0.0, help="modified Newton: keep a factor while steps "

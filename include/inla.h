@@ -130,6 +130,9 @@ typedef struct {
                           once the step (infinity norm) is below this; 0 = default (1e-2) */
   double reuse_shrink; /* ... and is kept while every step is at most this fraction of the one
                           before; 0 = default (0.25) */
+  int32_t var_slices;  /* INLA_MIXED: slices of the inverse of the factor at the mode, which gives
+                          the marginal variances (and their constraint correction): they need
+                          ~1e-4 relative where the log-determinant needs ~1e-8; 0 = `slices` */
 } inla_opts;
 
 typedef struct inla_model inla_model;   /* opaque; owns device copies of the model */

@@ -207,13 +207,18 @@ static int op_prior_dense(Batch& B) {
 }
 static int op_variances(Batch& B) {
   if (B.mixed) {
-    INLA_TRY(mixed_inverse_factor(B, SEL_L, true));
-    launch_rowsumsq_wk_df(B.d_slots, B.n, B.max_n, B.st);
-    if (B.max_k > 0) {
-      INLA_TRY(mixed_var_constraint(B));
-      launch_var_finish(B.d_slots, B.n, B.max_n, B.st);
+    // the inverse of the factor at the mode only feeds the variances (and, with the variational
+    // Bayes correction, the linear predictor's variances): its own slice count
+    const int S_keep = B.S;
+    B.S = B.S_var;
+    int rc = mixed_inverse_factor(B, SEL_L, true);
+    if (rc == INLA_OK) {
+      launch_rowsumsq_wk_df(B.d_slots, B.n, B.max_n, B.st);
+      if (B.max_k > 0 && (rc = mixed_var_constraint(B)) == INLA_OK)
+        launch_var_finish(B.d_slots, B.n, B.max_n, B.st);
     }
-    return INLA_OK;
+    B.S = S_keep;
+    return rc;
   }
   trtri64(B, SEL_L, DST_WK);
   launch_colsumsq_wk(B.d_slots, B.n, B.max_t, B.st);
@@ -782,10 +787,11 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   const int S_exact = mixed ? (o.slices == 0 ? 5 : o.slices) : 0;
   const int S_newton = mixed ? (o.newton_slices == 0 ? std::min(4, S_exact) : o.newton_slices) : 0;
   const int S_prior = mixed ? (o.prior_slices == 0 ? S_exact : o.prior_slices) : 0;
+  const int S_var = mixed ? (o.var_slices == 0 ? S_exact : o.var_slices) : 0;
   if (mixed && (S_exact < 2 || S_exact > OZ_MAX_S || S_newton < 2 || S_newton > OZ_MAX_S || S_prior < 2 ||
-                S_prior > OZ_MAX_S))
+                S_prior > OZ_MAX_S || S_var < 2 || S_var > OZ_MAX_S))
     return INLA_E_BADARG;
-  const int S = std::max(std::max(S_exact, S_newton), S_prior);  // workspace capacity
+  const int S = std::max(std::max(S_exact, S_newton), std::max(S_prior, S_var));  // workspace capacity
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
@@ -904,6 +910,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     Bt.S_exact = S_exact;
     Bt.S_newton = S_newton;
     Bt.S_prior = S_prior;
+    Bt.S_var = S_var;
     Bt.max_t = d0.n_pad / TB;
     Bt.max_td = d0.nd_pad / TB;
     Bt.max_tk = d0.k_pad / TB;

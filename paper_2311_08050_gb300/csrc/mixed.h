@@ -58,6 +58,7 @@ struct Batch {
   int S_exact = 0;       // prior inversion and the factor at the mode
   int S_newton = 0;      // Newton-step factorisations
   int S_prior = 0;       // prior covariance factorisation, inverse and W^T W
+  int S_var = 0;         // inverse of the factor at the mode (marginal variances)
   uint16_t *PA, *PB, *PBIG;
   int32_t *EA, *EB, *EBIG;
   int64_t pa_cap, pb_cap, pbig_cap;   // elements per slot

@@ -1,9 +1,11 @@
 """Full-size parity with the FP64 oracle, element by element, in the launch configuration the
 benchmark times (every point of a call batched together on the device):
 
-* the n = 16384 Poisson workload (9-point FD batch, mixed path as benchmarked), compared at
-  two FD points (the centre and the last axial point);
-* the constrained space-time model at full size (n = 8149, k = 1486), mixed path, one point;
+* the n = 16384 Poisson workload (9-point FD batch, mixed path as benchmarked: the slice counts
+  the precision autotuner picks for the model), compared at two FD points (the centre and the
+  last axial point);
+* the constrained space-time model at full size (n = 8149, k = 1486), mixed path with its tuned
+  slice counts, one point;
 * one Gaussian model of each size n in {512, 1024, 2048, 4096} from the 64-model workload,
   FP64 and mixed paths.
 
@@ -16,7 +18,7 @@ import pytest
 
 from oracle import inla_oracle as O
 from paper_2311_08050_gb300 import build as B
-from paper_2311_08050_gb300 import inla, synth
+from paper_2311_08050_gb300 import inla, synth, tune
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -40,7 +42,9 @@ def _errors(r, lp, x, v):
 def test_mixed_n16384_fd_batch_against_oracle_at_two_points():
     spec, thetas = synth.poisson_n16384_m100000_fd9()
     m = inla.Model(spec)
-    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed")
+    tr = tune.tune_precision(m, thetas[0])
+    print("n=16384 tuned slices", tr.opts())
+    lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed", **tr.opts())
     assert np.all(st == 0), st
     for b in (0, len(thetas) - 1):
         r = O.evaluate(spec, thetas[b])
@@ -54,7 +58,9 @@ def test_mixed_n16384_fd_batch_against_oracle_at_two_points():
 def test_mixed_spacetime_full_size_against_oracle():
     spec, thetas = synth.spacetime_n8149_m8000_fd13()
     m = inla.Model(spec)
-    lp, st, xs, vs = inla.eval_batch([m], thetas[:1], precision="mixed")
+    tr = tune.tune_precision(m, thetas[0])
+    print("space-time tuned slices", tr.opts())
+    lp, st, xs, vs = inla.eval_batch([m], thetas[:1], precision="mixed", **tr.opts())
     assert st[0] == 0, inla.status_string(st[0])
     r = O.evaluate(spec, thetas[0])
     e_lp, e_x, e_v = _errors(r, lp[0], xs[0], vs[0])
