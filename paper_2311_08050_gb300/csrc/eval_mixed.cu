@@ -97,6 +97,14 @@ class Side {
     res_ = &r;
   }
   ~Side() { join(); }
+  bool on() const { return res_ != nullptr; }
+  // a side launch that a later Side (the next tile's) joins: the side stream keeps its order
+  cudaStream_t fork_detached() {
+    if (!res_) return main_;
+    cudaEventRecord(res_->fork, main_);
+    cudaStreamWaitEvent(res_->st, res_->fork, 0);
+    return res_->st;
+  }
   // the stream for the side launch (ordered after everything issued so far on the batch's stream)
   cudaStream_t fork() {
     if (!res_) return main_;
@@ -153,8 +161,28 @@ static int mixed_panel(Batch& B, const MRef& M, int c0, int c1) {
   oz_slice_df(M.base, M.stride, M.ld, mid, c0, R, K, false, px, S, B.n, B.st);
   OzOperand pxt = px;
   pxt.rows = w;
-  OzArgs u = gemm_args(B, M.base + (int64_t)mid * M.ld + mid, M.stride, M.ld, R, w, K, 1.f, -1.f);
-  INLA_TRY(oz_gemm(px, pxt, u, B.n, B.st));
+  float2* C0 = M.base + (int64_t)mid * M.ld + mid;
+  Side side(B);
+  if (side.on() && R > IB) {
+    // Look-ahead: the next diagonal tile's 64 rows first (its factorisation needs only them); the
+    // other rows on the side stream, with one SM per slot left to the tile's factorisation, which
+    // runs meanwhile.  The next tile's panel is sliced on the side stream after them, and the tile
+    // joins the side stream before its triangular-solve product.
+    OzOperand pxa = px;
+    pxa.rows = IB;
+    OzArgs ua = gemm_args(B, C0, M.stride, M.ld, IB, w, K, 1.f, -1.f);
+    INLA_TRY(oz_gemm(pxa, pxt, ua, B.n, B.st));
+    OzOperand pxb = px;
+    pxb.planes += (int64_t)IB * px.ld_k;
+    pxb.exps += IB;
+    pxb.rows = R - IB;
+    OzArgs ub = gemm_args(B, C0 + (int64_t)IB * M.ld, M.stride, M.ld, R - IB, w, K, 1.f, -1.f);
+    ub.max_ctas = std::max(1, oz_num_sms() - B.n);
+    INLA_TRY(oz_gemm(pxb, pxt, ub, B.n, side.fork_detached()));
+  } else {
+    OzArgs u = gemm_args(B, C0, M.stride, M.ld, R, w, K, 1.f, -1.f);
+    INLA_TRY(oz_gemm(px, pxt, u, B.n, B.st));
+  }
   return mixed_panel(B, M, mid, c1);
 }
 

@@ -700,6 +700,8 @@ static int num_sms() {
   return v;
 }
 
+int oz_num_sms() { return num_sms(); }
+
 // Persistent launch: one CTA per SM (shared memory allows no second), tiles round-robin.
 template <int S, int BN>
 static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs& a, int nslots, cudaStream_t st) {
@@ -712,7 +714,8 @@ static int launch_oz(const CUtensorMap& ma, const CUtensorMap& mb, const OzArgs&
     attr_set.set(dev);
   }
   if (a.tiles_total <= 0) return INLA_OK;
-  const int grid = std::min(a.tiles_total, num_sms());
+  const int sms = num_sms();
+  const int grid = std::min(a.tiles_total, a.max_ctas > 0 ? std::min(a.max_ctas, sms) : sms);
   count_launch("k_ozaki_gemm<S>"), k_ozaki_gemm<S, BN><<<grid, OZ_THREADS, smem, st>>>(ma, mb, a);
   if (cudaPeekAtLastError() != cudaSuccess) return note_launch_error("k_ozaki_gemm launch");
   if (debug_sync_enabled()) {

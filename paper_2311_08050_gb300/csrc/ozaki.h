@@ -81,6 +81,7 @@ struct OzArgs {
   int S;
   int64_t spin_limit;
   int32_t* err;      // device flag: set to nonzero on a timed-out wait
+  int max_ctas;      // persistent grid cap (0: one CTA per SM), leaving SMs to concurrent kernels
 };
 
 // Host: encode a 3-D tensor map over an operand's planes (box OZ_KS x box_rows x S: all S
@@ -88,6 +89,8 @@ struct OzArgs {
 int oz_make_map(CUtensorMap* map, const OzOperand& op, int nplanes, int S, int box_rows);
 // Host: C = alpha C + beta A B^T for `nslots` slots (grid.z), S slices.
 int oz_gemm(const OzOperand& A, const OzOperand& B, const OzArgs& args, int nslots, cudaStream_t st);
+// Host: the SM count of the current device (the persistent grid)
+int oz_num_sms();
 
 // Slicing kernels (host launchers).  Source element (r, k) of operand row r is
 //   rows:  src[(row0 + r) * ld + col0 + k]      cols: src[(row0 + k) * ld + col0 + r]
