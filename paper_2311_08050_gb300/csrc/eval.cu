@@ -299,7 +299,7 @@ static void set_factor_ptrs(Slot& dst, const Slot& src) {
 // A^T diag(exp(eta)) A + Q_p well: fewer Newton factorisations than from x = 0.
 static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts& o, int* status, int* iters,
                         int* converged, int* d_flags, bool start_shared, const std::vector<Slot>& own,
-                        bool wls_start = false) {
+                        bool wls_start = false, bool* handed_over = nullptr) {
   const int NB = V.n;
   std::vector<double> out;
   std::vector<int32_t> info;
@@ -348,8 +348,6 @@ static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts
     int nact = 0;
     for (int i = 0; i < NB; ++i) nact += V.h[i].active;
     if (nact == 0) break;
-    for (int i = 0; i < NB; ++i)
-      if (V.h[i].active) iters[i] = it;
     // Q* = Q_p + A^T D A at x ; gradient ; factor ; Newton direction.  The mixed path reuses the
     // last factor once the steps are small and shrinking fast (modified Newton): the gradient
     // stays exact, so the fixed point is unchanged; a reused step that does not shrink the step
@@ -365,7 +363,15 @@ static int newton_phase(Batch& V, const ModelDev* const* models, const inla_opts
       }
     } else {
       refactor = !V.mixed || it - it_own < 2 || last_step > o.reuse_below || !reuse_ok;
+      // hand-over: the slots' own factor will now be kept (modified Newton near the mode), so the
+      // caller can run the remaining iterations together with other points that share it
+      if (handed_over && !refactor && it_own > 0) {
+        *handed_over = true;
+        break;
+      }
     }
+    for (int i = 0; i < NB; ++i)
+      if (V.h[i].active) iters[i] = it;
     if (refactor) op_assemble_q(V);
     launch_gradient(V.d_slots, NB, V.max_n, V.st);
     if ((rc = debug_check(V.st, "newton assemble")) != INLA_OK) break;
@@ -542,12 +548,17 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
   g_newton_trace.clear();
   int rc = INLA_OK;
   // ---------------- Newton, leaders ----------------
+  // With followers, the leaders stop as soon as they would keep their factor for the remaining
+  // (modified Newton) iterations: those then run in one batch with the followers, which start from
+  // their anchor's iterate with its factor, and every mode is factored in one batched call.
   prof_phase("newton_lead");
+  const bool followers = nlead < NB;
+  bool handed = false;
   {
     Batch V = view_of(B, 0, nlead);
     std::vector<Slot> own(V.h);
     rc = newton_phase(V, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, false, own,
-                      V.mixed && !(o.flags & INLA_OPT_NO_SHARED_START));
+                      V.mixed && !(o.flags & INLA_OPT_NO_SHARED_START), followers && V.mixed ? &handed : nullptr);
     copy_back(B, V, 0);
   }
   // a point that failed or did not converge leaves the rest of the evaluation
@@ -557,9 +568,57 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
       B.h[i].active = status[i] == INLA_OK;
     }
   };
-  if (rc == INLA_OK) settle(0, nlead);
-  // ---------------- factor at the leaders' modes; followers from their anchors ----------------
-  if (rc == INLA_OK && nlead < NB) {
+  if (rc == INLA_OK && followers && handed) {
+    // the leaders stopped with a factor of their own near their modes: they finish their
+    // (modified Newton) iterations in one batch with the followers, which start from their
+    // anchor's iterate with that factor; then every mode is factored in one batched call
+    for (int i = 0; i < nlead; ++i) B.h[i].active = status[i] == INLA_OK && !converged[i];
+    sync_active(B);
+    bool anchors_ok = true;
+    for (int i = nlead; i < NB; ++i) anchors_ok = anchors_ok && status[anchor_of[i]] == INLA_OK;
+    // the leaders' iterations before the hand-over, added to those after it
+    std::vector<int> iters_lead(iters.begin(), iters.begin() + nlead), cont(nlead);
+    for (int i = 0; i < nlead; ++i) cont[i] = B.h[i].active;
+    if (anchors_ok) {
+      std::vector<Slot> own(B.h);
+      for (int i = nlead; i < NB; ++i) {
+        if (!B.h[i].active) continue;
+        Slot& f = B.h[i];
+        const Slot& a = B.h[anchor_of[i]];
+        cudaMemcpyAsync(f.x, a.x, sizeof(double) * f.n_pad, cudaMemcpyDeviceToDevice, B.st);
+        set_factor_ptrs(f, a);
+      }
+      sync_active(B);
+      prof_phase("newton_follow");
+      rc = newton_phase(B, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, true, own);
+    } else {
+      // an anchor failed: the leaders finish on their own, the followers start from zero
+      {
+        Batch V = view_of(B, 0, nlead);
+        std::vector<Slot> own(V.h);
+        rc = newton_phase(V, models.data(), o, status.data(), iters.data(), converged.data(), d_flags, true, own);
+        copy_back(B, V, 0);
+      }
+      if (rc == INLA_OK) {
+        Batch F = view_of(B, nlead, NB);
+        std::vector<Slot> own(F.h);
+        prof_phase("newton_follow");
+        rc = newton_phase(F, models.data() + nlead, o, status.data() + nlead, iters.data() + nlead,
+                          converged.data() + nlead, d_flags, false, own);
+        copy_back(B, F, nlead);
+      }
+    }
+    for (int i = 0; i < nlead; ++i)
+      if (cont[i]) iters[i] += iters_lead[i];
+    if (rc == INLA_OK) {
+      settle(0, NB);
+      prof_phase("factor_modes");
+      rc = final_factor(B);
+    }
+  } else if (rc == INLA_OK && followers) {
+    // the leaders converged on their start-system factor: their factor at the mode first, then
+    // the followers from their anchor's mode with that factor
+    settle(0, nlead);
     prof_phase("factor_lead");
     Batch V = view_of(B, 0, nlead);
     rc = final_factor(V);
@@ -592,6 +651,7 @@ static int run_batch(Batch& B, const std::vector<const ModelDev*>& models, const
       }
     }
   } else if (rc == INLA_OK) {
+    settle(0, nlead);
     prof_phase("factor_lead");
     rc = final_factor(B);
   }

@@ -177,7 +177,7 @@ def test_newton_trace_refactors_early_and_reuses_near_the_mode():
             assert np.all(ref[:n] == 1)
         else:
             assert ref[n - 1] == 0       # the last iterations reuse the factor
-            assert np.sum(ref[:n]) < n // 2
+            assert np.sum(ref[:n]) <= n // 2  # at most every other iteration factors afresh
 
 
 def _check_vs_fp64(lp, st, xs, vs, ref, names):
