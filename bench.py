@@ -205,7 +205,7 @@ def run_ours(args):
     vp = [vbuf[b].data_ptr() for b in range(nb)]
     kw = dict(precision=args.precision, slices=args.slices, newton_slices=args.newton_slices, stream=sptr,
               device_out=True, x_out=xp, var_out=vp, prior_slices=args.prior_slices, reuse_below=args.reuse_below,
-              reuse_shrink=args.reuse_shrink, var_slices=args.var_slices)
+              reuse_shrink=args.reuse_shrink, var_slices=args.var_slices, gram_slices=args.gram_slices)
 
     def step():
         lp, st, _, _ = inla.eval_batch([model], thetas, **kw)
@@ -224,9 +224,9 @@ def run_ours(args):
         tr = tune.tune_precision(model, thetas[0], stream=sptr)
         kw.update(tr.opts())
         args.slices, args.newton_slices, args.prior_slices = tr.slices, tr.newton_slices, tr.prior_slices
-        args.var_slices = tr.var_slices
-        tuned = {"prior_slices": tr.prior_slices, "slices": tr.slices, "newton_slices": tr.newton_slices,
-                 "var_slices": tr.var_slices,
+        args.var_slices, args.gram_slices = tr.var_slices, tr.gram_slices
+        tuned = {"prior_slices": tr.prior_slices, "gram_slices": tr.gram_slices, "slices": tr.slices,
+                 "newton_slices": tr.newton_slices, "var_slices": tr.var_slices,
                  "errors_vs_six_slices": tr.errors, "tuning_seconds": round(tr.seconds, 2),
                  "tried": [t["setting"] for t in tr.tried]}
     for _ in range(max(1, args.warmup)):
@@ -326,7 +326,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": f"bf16 Ozaki slices x{args.prior_slices or args.slices} (prior) / x{args.slices} (final factor) / "
+           "dtype": f"bf16 Ozaki slices x{args.prior_slices or args.slices} (prior factor and inverse) / "
+                    f"x{args.gram_slices or args.prior_slices or args.slices} (prior precision W^T W) / x{args.slices} (final factor) / "
                     f"x{args.var_slices or args.slices} (its inverse: variances) / x{args.newton_slices} (Newton), "
                     "exact fp32 accumulation + df64 storage and diagonal tiles"
            if args.precision == "mixed" else "f64",
@@ -335,6 +336,7 @@ def run_ours(args):
                       "precision": args.precision, "slices": args.slices, "newton_slices": args.newton_slices,
                       "prior_slices": args.prior_slices or args.slices,
                       "var_slices": args.var_slices or args.slices,
+                      "gram_slices": args.gram_slices or args.prior_slices or args.slices,
                       "reuse_below": args.reuse_below or 1e-2, "reuse_shrink": args.reuse_shrink or 0.25,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "outer_block_tuned": outer_block, "precision_tuned": tuned,
@@ -354,7 +356,7 @@ def run_ours(args):
             lp2, st2, xs2, vs2 = inla.eval_batch([m2], pthetas, precision=args.precision, slices=args.slices,
                                                  newton_slices=args.newton_slices, prior_slices=args.prior_slices,
                                                  reuse_below=args.reuse_below, reuse_shrink=args.reuse_shrink,
-                                                 var_slices=args.var_slices)
+                                                 var_slices=args.var_slices, gram_slices=args.gram_slices)
             m2.close()
         t_e2e = time.perf_counter() - t0
         out["e2e"] = {"value": nb * e2e_steps / t_e2e * world, "unit": UNIT,
@@ -587,6 +589,8 @@ def main():
                     help="use the given slice counts instead of the autotuned rungs")
     ap.add_argument("--newton-slices", type=int, default=4, help="slices of the Newton-step factorisations")
     ap.add_argument("--prior-slices", type=int, default=0, help="slices of the prior inversion (0: --slices)")
+    ap.add_argument("--gram-slices", type=int, default=0,
+                    help="slices of the prior precision W^T W (0: --prior-slices)")
     ap.add_argument("--var-slices", type=int, default=0,
                     help="slices of the inverse of the factor at the mode, for the variances (0: --slices)")
     ap.add_argument("--reuse-below", type=float, default=0.0, help="modified Newton: reuse a factor once steps are "

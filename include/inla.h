@@ -124,8 +124,8 @@ typedef struct {
   int64_t spin_limit;  /* iteration limit of every device-side wait (default 1<<26) */
   void *stream;        /* cudaStream_t to run on, or NULL for the default stream */
   int32_t flags;       /* INLA_OPT_* */
-  int32_t prior_slices;  /* INLA_MIXED: slices of the prior covariance factorisation and inverse;
-                          0 = `slices` */
+  int32_t prior_slices;  /* INLA_MIXED: slices of the prior covariance's factorisation and of the
+                          triangular inverse W of its factor; 0 = `slices` */
   double reuse_below;  /* INLA_MIXED modified Newton: a factor may be kept for later iterations
                           once the step (infinity norm) is below this; 0 = default (1e-2) */
   double reuse_shrink; /* ... and is kept while every step is at most this fraction of the one
@@ -133,6 +133,9 @@ typedef struct {
   int32_t var_slices;  /* INLA_MIXED: slices of the inverse of the factor at the mode, which gives
                           the marginal variances (and their constraint correction): they need
                           ~1e-4 relative where the log-determinant needs ~1e-8; 0 = `slices` */
+  int32_t gram_slices; /* INLA_MIXED: slices of the prior precision Q_p = W^T W, which enters log pi~
+                          directly (the factorisation and inverse before it only perturb the
+                          covariance, whose effect is far smaller); 0 = `prior_slices` */
 } inla_opts;
 
 typedef struct inla_model inla_model;   /* opaque; owns device copies of the model */

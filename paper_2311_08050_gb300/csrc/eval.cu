@@ -196,7 +196,11 @@ static int op_prior_dense(Batch& B) {
     INLA_TRY(mixed_potrf(B, SEL_COV));
     launch_logdet_df(B.d_slots, B.n, SEL_COV, OUT_LOGDET_COV, B.st);
     INLA_TRY(mixed_inverse_factor(B, SEL_COV, false));
-    return mixed_lauum_cov(B);
+    const int S_keep = B.S;
+    B.S = B.S_gram;  // Q_p itself: its own slice count
+    const int rc = mixed_lauum_cov(B);
+    B.S = S_keep;
+    return rc;
   }
   launch_cov_build(B.d_slots, B.n, B.max_td, B.st);
   potrf64(B, SEL_COV);
@@ -848,10 +852,11 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   const int S_newton = mixed ? (o.newton_slices == 0 ? std::min(4, S_exact) : o.newton_slices) : 0;
   const int S_prior = mixed ? (o.prior_slices == 0 ? S_exact : o.prior_slices) : 0;
   const int S_var = mixed ? (o.var_slices == 0 ? S_exact : o.var_slices) : 0;
+  const int S_gram = mixed ? (o.gram_slices == 0 ? S_prior : o.gram_slices) : 0;
   if (mixed && (S_exact < 2 || S_exact > OZ_MAX_S || S_newton < 2 || S_newton > OZ_MAX_S || S_prior < 2 ||
-                S_prior > OZ_MAX_S || S_var < 2 || S_var > OZ_MAX_S))
+                S_prior > OZ_MAX_S || S_var < 2 || S_var > OZ_MAX_S || S_gram < 2 || S_gram > OZ_MAX_S))
     return INLA_E_BADARG;
-  const int S = std::max(std::max(S_exact, S_newton), std::max(S_prior, S_var));  // workspace capacity
+  const int S = std::max(std::max(std::max(S_exact, S_newton), std::max(S_prior, S_var)), S_gram);  // workspace
   cudaStream_t st = static_cast<cudaStream_t>(o.stream);
   prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
@@ -971,6 +976,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
     Bt.S_newton = S_newton;
     Bt.S_prior = S_prior;
     Bt.S_var = S_var;
+    Bt.S_gram = S_gram;
     Bt.max_t = d0.n_pad / TB;
     Bt.max_td = d0.nd_pad / TB;
     Bt.max_tk = d0.k_pad / TB;

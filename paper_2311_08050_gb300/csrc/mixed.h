@@ -59,6 +59,7 @@ struct Batch {
   int S_newton = 0;      // Newton-step factorisations
   int S_prior = 0;       // prior covariance factorisation, inverse and W^T W
   int S_var = 0;         // inverse of the factor at the mode (marginal variances)
+  int S_gram = 0;        // the prior precision W^T W
   uint16_t *PA, *PB, *PBIG;
   int32_t *EA, *EB, *EBIG;
   int64_t pa_cap, pb_cap, pbig_cap;   // elements per slot

@@ -57,7 +57,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", _i32), ("slices", _i32), ("newton_slices", _i32), ("newton_tol", _d),
                 ("newton_max", _i32),
                 ("spin_limit", _i64), ("stream", C.c_void_p), ("flags", _i32), ("prior_slices", _i32),
-                ("reuse_below", _d), ("reuse_shrink", _d), ("var_slices", _i32)]
+                ("reuse_below", _d), ("reuse_shrink", _d), ("var_slices", _i32), ("gram_slices", _i32)]
 
 
 _lib = None
@@ -99,7 +99,7 @@ def _ptr(a, ct):
 
 def make_opts(precision="fp64", slices=0, newton_tol=1e-8, newton_max=50, stream=None, device_out=False,
               spin_limit=1 << 26, newton_slices=0, flags_extra=0, prior_slices=0, reuse_below=0.0,
-              reuse_shrink=0.0, var_slices=0):
+              reuse_shrink=0.0, var_slices=0, gram_slices=0):
     o = Opts()
     lib().inla_opts_default(C.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -114,6 +114,7 @@ def make_opts(precision="fp64", slices=0, newton_tol=1e-8, newton_max=50, stream
     o.reuse_below = reuse_below
     o.reuse_shrink = reuse_shrink
     o.var_slices = var_slices
+    o.gram_slices = gram_slices
     return o
 
 

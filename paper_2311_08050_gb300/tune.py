@@ -1,7 +1,8 @@
 """Precision-rung autotuner of the mixed path.
 
 The mixed path's accuracy is set by its slice counts: ``prior_slices`` (the prior covariance's
-factorisation, inverse and W^T W), ``slices`` (the factor at the mode: log|Q*|), ``var_slices``
+factorisation and the inverse W of its factor), ``gram_slices`` (the prior precision W^T W),
+``slices`` (the factor at the mode: log|Q*|), ``var_slices``
 (the inverse of that factor, which gives the marginal variances) and ``newton_slices`` (the
 Newton-step factorisations, which only steer the iteration: the gradient is exact).  Each slice
 adds 7 bits and costs passes of the tensor-core GEMM (S (S + 1) / 2 BF16 products per GEMM), so
@@ -22,17 +23,20 @@ import numpy as np
 
 from . import inla
 
-# (prior_slices, slices, newton_slices, var_slices) from the cheapest up, by the GEMM passes
-# S (S + 1) / 2 weighted with each phase's share of the algorithmic flops of an FD batch: the prior
-# inversion n^3, the factor at the mode n^3 / 3, the inverse of that factor n^3 / 3, the Newton
-# factorisations of the leading point ~0.2 n^3 per point
-CANDIDATES = [(4, 4, 3, 3), (4, 4, 3, 4), (4, 5, 3, 4), (4, 4, 4, 4), (5, 4, 3, 3), (5, 4, 3, 4), (5, 5, 3, 3),
-              (5, 5, 3, 4), (5, 5, 3, 5), (5, 5, 4, 4), (5, 5, 4, 5), (6, 5, 4, 5), (6, 6, 4, 6)]
+# (prior_slices, gram_slices, slices, newton_slices, var_slices) from the cheapest up, by the GEMM
+# passes S (S + 1) / 2 weighted with each phase's share of the algorithmic flops of an FD batch:
+# the prior covariance's factorisation and inverse 2 n^3 / 3, the product W^T W n^3 / 3, the
+# factor at the mode n^3 / 3, its inverse n^3 / 3, the leading point's Newton factorisations
+# ~0.2 n^3 per point
+CANDIDATES = [(4, 4, 4, 3, 3), (4, 4, 4, 3, 4), (4, 5, 4, 3, 4), (4, 4, 5, 3, 4), (4, 5, 5, 3, 3), (4, 4, 4, 4, 4),
+              (4, 5, 5, 3, 4), (5, 5, 4, 3, 4), (5, 5, 5, 3, 3), (4, 5, 5, 4, 4), (5, 5, 5, 3, 4), (5, 5, 5, 3, 5),
+              (5, 5, 5, 4, 4), (5, 5, 5, 4, 5), (6, 6, 5, 4, 5), (6, 6, 6, 4, 6)]
 
 
 @dataclass
 class TuneResult:
     prior_slices: int
+    gram_slices: int
     slices: int
     newton_slices: int
     var_slices: int
@@ -41,8 +45,8 @@ class TuneResult:
     seconds: float = 0.0
 
     def opts(self):
-        return dict(prior_slices=self.prior_slices, slices=self.slices, newton_slices=self.newton_slices,
-                    var_slices=self.var_slices)
+        return dict(prior_slices=self.prior_slices, gram_slices=self.gram_slices, slices=self.slices,
+                    newton_slices=self.newton_slices, var_slices=self.var_slices)
 
 
 _cache: dict = {}
@@ -57,7 +61,7 @@ def _errors(ref, cand):
 
 
 def tune_precision(model, theta, lp_abs=1e-3, var_rel=1e-4, x_rel=1e-4, margin=3.0, **opt_kw):
-    """The cheapest (prior_slices, slices, newton_slices, var_slices) whose errors against the six-slice
+    """The cheapest (prior_slices, gram_slices, slices, newton_slices, var_slices) whose errors against the six-slice
     evaluation of `theta` are within (targets / margin).  opt_kw: stream and other options
     passed to every evaluation."""
     key = (id(model), tuple(np.round(np.asarray(theta, dtype=np.float64), 12)), lp_abs, var_rel, x_rel, margin)
@@ -66,31 +70,31 @@ def tune_precision(model, theta, lp_abs=1e-3, var_rel=1e-4, x_rel=1e-4, margin=3
     t0 = time.perf_counter()
     th = np.asarray(theta, dtype=np.float64)[None, :]
 
-    def run(p, s, nw, v):
-        lp, st, xs, vs = inla.eval_batch([model], th, precision="mixed", prior_slices=p, slices=s, newton_slices=nw,
-                                         var_slices=v, **opt_kw)
+    def run(p, g, s, nw, v):
+        lp, st, xs, vs = inla.eval_batch([model], th, precision="mixed", prior_slices=p, gram_slices=g, slices=s,
+                                         newton_slices=nw, var_slices=v, **opt_kw)
         if st[0] != 0:
             return None
         return float(lp[0]), xs[0], vs[0]
 
-    ref = run(6, 6, 4, 6)
+    ref = run(6, 6, 6, 4, 6)
     if ref is None:
         raise RuntimeError("reference evaluation failed")
     tried = []
     chosen = None
-    for p, s, nw, v in CANDIDATES:
-        r = run(p, s, nw, v)
+    for p, g, s, nw, v in CANDIDATES:
+        r = run(p, g, s, nw, v)
         if r is None:
-            tried.append({"setting": (p, s, nw, v), "status": "failed"})
+            tried.append({"setting": (p, g, s, nw, v), "status": "failed"})
             continue
         e = _errors(ref, r)
         ok = e["log_post_abs"] <= lp_abs / margin and e["var_rel"] <= var_rel / margin and e["x_hat_rel"] <= x_rel / margin
-        tried.append({"setting": (p, s, nw, v), "errors": e, "ok": bool(ok)})
+        tried.append({"setting": (p, g, s, nw, v), "errors": e, "ok": bool(ok)})
         if ok:
-            chosen = TuneResult(p, s, nw, v, e)
+            chosen = TuneResult(p, g, s, nw, v, e)
             break
     if chosen is None:
-        chosen = TuneResult(6, 6, 4, 6, {"log_post_abs": 0.0, "x_hat_rel": 0.0, "var_rel": 0.0})
+        chosen = TuneResult(6, 6, 6, 4, 6, {"log_post_abs": 0.0, "x_hat_rel": 0.0, "var_rel": 0.0})
     chosen.tried = tried
     chosen.seconds = time.perf_counter() - t0
     _cache[key] = chosen

@@ -287,7 +287,7 @@ def test_precision_autotuner_choice_meets_the_targets_against_the_oracle():
     m = inla.Model(spec)
     tr = tune.tune_precision(m, thetas[0])
     print("tuned", tr.opts(), tr.errors, [t["setting"] for t in tr.tried])
-    assert (tr.prior_slices, tr.slices, tr.newton_slices, tr.var_slices) in tune.CANDIDATES
+    assert (tr.prior_slices, tr.gram_slices, tr.slices, tr.newton_slices, tr.var_slices) in tune.CANDIDATES
     passes = lambda S: S * (S + 1) // 2
     assert passes(tr.prior_slices) + passes(tr.slices) <= passes(5) + passes(5)
     lp, st, xs, vs = inla.eval_batch([m], thetas, precision="mixed", **tr.opts())
