@@ -122,7 +122,9 @@ typedef struct {
   double newton_tol;   /* infinity-norm step tolerance (default 1e-8) */
   int32_t newton_max;  /* maximum Newton iterations (default 50) */
   int64_t spin_limit;  /* iteration limit of every device-side wait (default 1<<26) */
-  void *stream;        /* cudaStream_t to run on, or NULL for the default stream */
+  void *stream;        /* cudaStream_t to run on, or NULL: the library's own stream of the current
+                          device, ordered after the work queued on the legacy default stream
+                          before the call and before the work queued there after it */
   int32_t flags;       /* INLA_OPT_* */
   int32_t prior_slices;  /* INLA_MIXED: slices of the prior covariance's factorisation and of the
                           triangular inverse W of its factor; 0 = `slices` */

@@ -831,6 +831,54 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
   return cv.off;
 }
 
+// A call without a stream runs on the library's own non-blocking stream of the device (CUDA graphs
+// and side streams need a capturable stream; the legacy default stream is not one), ordered after
+// the work queued on the legacy default stream before the call and before the work queued there
+// after it (events both ways, on every return path).
+namespace {
+struct OwnStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+};
+OwnStream g_own_stream[64];
+std::mutex g_own_mu;
+class LegacyBridge {
+ public:
+  // the stream to run on: `requested`, or the device's own stream when it is NULL
+  cudaStream_t begin(cudaStream_t requested) {
+    if (requested) return requested;
+    const int dev = current_device();
+    if (dev < 0 || dev >= 64) return requested;
+    std::lock_guard<std::mutex> lk(g_own_mu);
+    OwnStream& r = g_own_stream[dev];
+    if (!r.st) {
+      OwnStream n;
+      if (cudaStreamCreateWithFlags(&n.st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&n.in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&n.out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return requested;  // stays on the legacy stream
+      }
+      r = n;
+    }
+    if (cudaEventRecord(r.in, 0) != cudaSuccess || cudaStreamWaitEvent(r.st, r.in, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return requested;
+    }
+    res_ = &r;
+    return r.st;
+  }
+  ~LegacyBridge() {
+    if (!res_) return;
+    cudaEventRecord(res_->out, res_->st);
+    cudaStreamWaitEvent(0, res_->out, 0);
+  }
+
+ private:
+  OwnStream* res_ = nullptr;
+};
+}  // namespace
+
 static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int32_t* model_of_theta,
                            const double* thetas, int32_t B_, const inla_opts* opts_in, double* log_post,
                            int32_t* status_out, double* const* x_hat, double* const* var,
@@ -857,7 +905,8 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
                 S_prior > OZ_MAX_S || S_var < 2 || S_var > OZ_MAX_S || S_gram < 2 || S_gram > OZ_MAX_S))
     return INLA_E_BADARG;
   const int S = std::max(std::max(std::max(S_exact, S_newton), std::max(S_prior, S_var)), S_gram);  // workspace
-  cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+  LegacyBridge bridge;
+  cudaStream_t st = bridge.begin(static_cast<cudaStream_t>(o.stream));
   prof_set_stream(st);
   const bool dev_out = (o.flags & INLA_OPT_DEVICE_OUT) != 0;
   const bool want_var = var != nullptr;
