@@ -337,7 +337,7 @@ def run_ours(args):
                       "prior_slices": args.prior_slices or args.slices,
                       "var_slices": args.var_slices or args.slices,
                       "gram_slices": args.gram_slices or args.prior_slices or args.slices,
-                      "reuse_below": args.reuse_below or 1e-2, "reuse_shrink": args.reuse_shrink or 0.25,
+                      "reuse_below": args.reuse_below or 0.1, "reuse_shrink": args.reuse_shrink or 0.25,
                       "l2": "inputs larger than L2 (2 GiB double-float matrices per theta)",
                       "outer_block_tuned": outer_block, "precision_tuned": tuned,
                       "parallelism": f"{world} GPU(s), theta batches sharded across ranks"},

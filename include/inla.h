@@ -129,7 +129,7 @@ typedef struct {
   int32_t prior_slices;  /* INLA_MIXED: slices of the prior covariance's factorisation and of the
                           triangular inverse W of its factor; 0 = `slices` */
   double reuse_below;  /* INLA_MIXED modified Newton: a factor may be kept for later iterations
-                          once the step (infinity norm) is below this; 0 = default (1e-2) */
+                          once the step (infinity norm) is below this; 0 = default (0.1) */
   double reuse_shrink; /* ... and is kept while every step is at most this fraction of the one
                           before; 0 = default (0.25) */
   int32_t var_slices;  /* INLA_MIXED: slices of the inverse of the factor at the mode, which gives

@@ -891,7 +891,7 @@ static int eval_batch_impl(inla_model* const* models, int32_t nmodels, const int
   if (o.newton_tol <= 0) o.newton_tol = 1e-8;
   if (o.newton_max <= 0) o.newton_max = 50;
   if (o.spin_limit <= 0) o.spin_limit = (int64_t)1 << 26;
-  if (!(o.reuse_below > 0)) o.reuse_below = 1e-2;
+  if (!(o.reuse_below > 0)) o.reuse_below = 0.1;
   if (!(o.reuse_shrink > 0)) o.reuse_shrink = 0.25;
   if (o.reuse_shrink >= 1.0) return INLA_E_BADARG;
   if (o.precision != INLA_FP64 && o.precision != INLA_MIXED) return INLA_E_BADARG;
@@ -1110,7 +1110,7 @@ extern "C" int inla_opts_default(inla_opts* o) {
   o->newton_tol = 1e-8;
   o->newton_max = 50;
   o->spin_limit = (int64_t)1 << 26;
-  o->reuse_below = 1e-2;
+  o->reuse_below = 0.1;
   o->reuse_shrink = 0.25;
   o->stream = nullptr;
   o->flags = 0;
