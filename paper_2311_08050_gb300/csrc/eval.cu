@@ -769,6 +769,7 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
   double* mvecs = cv.take<double>(G * m * (L.vb ? 3 : 2));
   double* pcov = L.vb ? cv.take<double>(G * std::max<int64_t>(L.npairs, 1)) : nullptr;
   double* red = cv.take<double>(G * 256);
+  double* qpart = L.mixed ? cv.take<double>(G * (np / TB) * np) : nullptr;
   double* outs = cv.take<double>(G * SLOT_NOUT);
   int32_t* infos = cv.take<int32_t>(G * 2);
   B.mixed = L.mixed;
@@ -824,6 +825,7 @@ static size_t carve_group(Carve& cv, const Layout& L, int G, Batch& B, std::vect
         s.pcov = pcov + i * std::max<int64_t>(L.npairs, 1);
       }
       s.red = red + i * 256;
+      s.qpart = qpart ? qpart + (size_t)i * (np / TB) * np : nullptr;
       s.out = outs + i * SLOT_NOUT;
       s.info = infos + i * 2;
     }

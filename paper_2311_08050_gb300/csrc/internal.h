@@ -152,6 +152,8 @@ struct Slot {
   // vectors
   double *x, *xn, *g, *t1, *t2;    // n_pad
   double *vd;                      // n_pad: double-float copy of a vector (mixed path)
+  double *qpart;                   // n_pad / 64 x n_pad: column sums of Q_p's tiles left of the
+                                   // diagonal (mixed path, symmetric Q_p v)
   double *vsave;                   // n_pad: the variances while the variational Bayes steps run
   double *eta, *w;                 // m
   double *etav;                    // m: variance of the linear predictor (variational Bayes)

@@ -155,21 +155,75 @@ __global__ void __launch_bounds__(256) k_vec_to_df(Slot* slots, int which) {
   for (int j = blockIdx.x * 256 + threadIdx.x; j < s.n_pad; j += gridDim.x * 256) df_store(dfm(s.vd) + j, df_from_double(v[j]));
 }
 
-// t1 = Q_p v (df64 Q_p, full symmetric; v from vd), one warp per row
-__global__ void __launch_bounds__(256) k_qp_gemv_df(Slot* slots, int which) {
+// t1 = Q_p v from the lower triangle of the symmetric Q_p (df64, stored mirrored; v from vd), so
+// that each element below the diagonal tiles is read once.  Block (tile row I, slot), the longest
+// rows first: each 64 x 64 tile (I, J <= I) is staged in shared memory; its row sums Q_IJ v_J
+// accumulate into t1's tile I (the diagonal tile in full), and for J < I its column sums
+// Q_IJ^T v_I go to qpart[I][tile J], which k_qp_symv_sum_df adds to t1's tile J in a fixed order.
+// Thread (row or column tid & 63, 16-wide quarter tid >> 6); the next tile is loaded into
+// registers while the current one is summed.
+__global__ void __launch_bounds__(256) k_qp_symv_part_df(Slot* slots) {
   const Slot& s = slots[blockIdx.y];
   if (!s.active) return;
-  (void)which;
+  const int n = s.n_pad, T = n / TB;
+  const int I = T - 1 - (int)blockIdx.x;
+  if (I < 0) return;
+  __shared__ float2 tile[TB][TB + 1];
+  __shared__ float2 vi[TB], vj[TB];
+  __shared__ float2 cpart[4][TB];
+  const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;
+  const float2* Q = dfm(s.Qp);
   const float2* vd = dfm(s.vd);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n = s.n_pad;
-  for (int row = blockIdx.x * 8 + warp; row < n; row += gridDim.x * 8) {
-    const float2* q = dfm(s.Qp) + (size_t)row * n;
-    df acc = df_make(0.f, 0.f);
-    for (int c = lane; c < n; c += 32) acc = df_fma(acc, df_load(q + c), df_load(vd + c));
-    double r = df_to_double(acc);
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (lane == 0) s.t1[row] = r;
+  if (tid < TB) vi[tid] = vd[I * TB + tid];
+  float2 nxt[16];
+  auto load = [&](int J) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) nxt[k] = Q[(size_t)(I * TB + k * 4 + q) * n + J * TB + r];
+  };
+  load(0);
+  df rowacc = df_make(0.f, 0.f);
+  for (int J = 0; J <= I; ++J) {
+    __syncthreads();  // the previous tile and its column sums are consumed
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tile[k * 4 + q][r] = nxt[k];
+    if (tid < TB) vj[tid] = vd[J * TB + tid];
+    __syncthreads();
+    if (J < I) load(J + 1);
+    df a = df_make(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a = df_add_fast(a, df_mul(df_load(&tile[r][q * 16 + c]), df_load(&vj[q * 16 + c])));
+    rowacc = df_add(rowacc, a);
+    if (J < I) {
+      df b = df_make(0.f, 0.f);
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) b = df_add_fast(b, df_mul(df_load(&tile[q * 16 + rr][r]), df_load(&vi[q * 16 + rr])));
+      cpart[q][r] = make_float2(b.hi, b.lo);
+      __syncthreads();
+      if (tid < TB) {
+        df c2 = df_load(&cpart[0][tid]);
+        for (int h = 1; h < 4; ++h) c2 = df_add(c2, df_load(&cpart[h][tid]));
+        s.qpart[(size_t)I * n + J * TB + tid] = df_to_double(c2);
+      }
+    }
+  }
+  __syncthreads();
+  cpart[q][r] = make_float2(rowacc.hi, rowacc.lo);
+  __syncthreads();
+  if (tid < TB) {
+    df t = df_load(&cpart[0][tid]);
+    for (int h = 1; h < 4; ++h) t = df_add(t, df_load(&cpart[h][tid]));
+    s.t1[I * TB + tid] = df_to_double(t);
+  }
+}
+// t1_j += sum over the tile rows I below j's tile of qpart[I][j], in increasing I
+__global__ void __launch_bounds__(256) k_qp_symv_sum_df(Slot* slots) {
+  const Slot& s = slots[blockIdx.y];
+  if (!s.active) return;
+  const int n = s.n_pad, T = n / TB;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) {
+    double a = 0.0;
+    for (int I = j / TB + 1; I < T; ++I) a += s.qpart[(size_t)I * n + j];
+    s.t1[j] += a;
   }
 }
 
@@ -646,7 +700,9 @@ void launch_add_pairs_df(Slot* slots, int nslots, int64_t max_pairs, cudaStream_
 }
 void launch_qp_gemv_df(Slot* slots, int nslots, int which, int max_n, cudaStream_t st) {
   count_launch("k_vec_to_df"), k_vec_to_df<<<dim3(vgrid(max_n), nslots), 256, 0, st>>>(slots, which);
-  count_launch("k_qp_gemv_df"), k_qp_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots, which);
+  (void)which;
+  count_launch("k_qp_symv_part_df"), k_qp_symv_part_df<<<dim3(max_n / TB, nslots), 256, 0, st>>>(slots);
+  count_launch("k_qp_symv_sum_df"), k_qp_symv_sum_df<<<dim3(std::min(1024, (max_n + 255) / 256), nslots), 256, 0, st>>>(slots);
 }
 void launch_z_gemv_df(Slot* slots, int nslots, int max_n, cudaStream_t st) {
   count_launch("k_z_gemv_df"), k_z_gemv_df<<<dim3(std::min(4096, (max_n + 7) / 8), nslots), 256, 0, st>>>(slots);
