@@ -263,17 +263,31 @@ __global__ void k_s_pad_identity(Slot* slots) {
 // Diagonal 64-tile: Cholesky factor and its inverse in double-float on the FP32 pipes (this
 // GPU's FP64 rate is ~2 FMA/clock/SM).  One CTA of DG_THREADS threads per tile, the tile in shared
 // memory (row pitch 65 cells).  Factor: right-looking elimination A = L1 D L1^T, step j
-// subtracting (a_ij / a_jj) a_cj from every a_ic with i >= c > j.  The elements of step j are the
-// first (63 - j)(64 - j) / 2 entries of a fixed table that lists the lower triangle by column,
-// last column first, so the threads share each step evenly (at most a few elements each, the
-// absent ones skipped uniformly); thread 0 only updates the next pivot a_{j+1,j+1} and publishes its
-// reciprocal, so one barrier per step closes it.  Then L = L1 D^1/2 is written out and L1 is
-// inverted in place by levels (s = 1, 2, .., 32: two inverted diagonal blocks of size s and the
-// block below them give the inverse of the 2s block, -Y22 L21 Y11), so L^-1 = D^-1/2 Y.  Stores
-// the factor tile (double-float, upper part zeroed) and the inverse tile (double-float, in the
-// FP64-sized cells of the inverse-tile array).
+// subtracting (a_ij / a_jj) a_cj from every a_ic with i >= c > j.  The lower triangle is listed by
+// column, last column first, rows ascending, so the elements step j updates are the first
+// (63 - j)(64 - j) / 2 positions of the list and column j + 1 is the last 64 - (j + 1) of them.
+// Thread t owns positions t, t + DG_THREADS, .. and keeps those elements in registers for the
+// whole elimination: at step j it reads a_ij and a_cj (column j, final) from shared memory, and
+// publishes an element there once it is final (when its column is j + 1); the owner of the next
+// pivot a_{j+1,j+1} also publishes its reciprocal, so one barrier per step closes it and warps
+// whose positions are all past the step's prefix only meet the barrier.  Then L = L1 D^1/2 is
+// written out and L1 is inverted in place by levels (s = 1, 2, .., 32: two inverted diagonal
+// blocks of size s and the block below them give the inverse of the 2s block, -Y22 L21 Y11), so
+// L^-1 = D^-1/2 Y.  Stores the factor tile (double-float, upper part zeroed) and the inverse tile
+// (double-float, in the FP64-sized cells of the inverse-tile array).
 constexpr int DG_LD = TB + 1;
 constexpr int DG_THREADS = 1024;
+// 1 / a for the tile's pivot chain: the PTX approximate reciprocal (within 1 ulp over the whole
+// FP32 range) refined by one Newton step r0 + r0 (1 - a r0) in double-float, ~2^-44 relative;
+// ~17 cycles shorter than an IEEE-rounded seed on every elimination step
+__device__ __forceinline__ df dg_recip(df a) {
+  float r0;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(a.hi));
+  const float e = __fmaf_rn(-a.lo, r0, __fmaf_rn(-a.hi, r0, 1.0f));
+  float s, t;
+  fast_two_sum(r0, r0 * e, s, t);
+  return df{s, t};
+}
 __device__ __forceinline__ df dg_ld(const float2* t, int i, int c) { return df_make(t[i * DG_LD + c].x, t[i * DG_LD + c].y); }
 __device__ __forceinline__ void dg_st(float2* t, int i, int c, df v) { t[i * DG_LD + c] = make_float2(v.hi, v.lo); }
 
@@ -283,9 +297,8 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
   DfRef M = df_ref(s, sel);
   if (kt * TB >= M.n) return;
   constexpr int NTRI = TB * (TB + 1) / 2;  // 2080 lower-triangle elements (diagonal included)
-  constexpr int NW = DG_THREADS - 1;       // threads sharing the elements of a step
+  constexpr int NQ = (NTRI + DG_THREADS - 1) / DG_THREADS;  // positions per thread
   __shared__ float2 t[TB * DG_LD];
-  __shared__ uint16_t tab[NTRI];           // (i << 8) | c, columns 63, 62, .., 0, rows ascending
   __shared__ float2 rpa[TB];               // 1 / a_jj
   __shared__ float2 dsq[TB], rdq[TB];      // sqrt(a_jj), 1 / sqrt(a_jj)
   __shared__ int bad_sh;
@@ -296,14 +309,6 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     const int i = e >> 6, c = e & 63;
     if (c <= i) t[i * DG_LD + c] = base[(size_t)i * M.ld + c];
   }
-  // table: column c (from 63 down) occupies positions [ (63-c)(64-c)/2, (64-c)(65-c)/2 )
-  for (int x = tid; x < TB * TB; x += DG_THREADS) {
-    const int c = x >> 6, i = x & 63;
-    if (i >= c) {
-      const int w = 63 - c;
-      tab[w * (w + 1) / 2 + (i - c)] = (uint16_t)((i << 8) | c);
-    }
-  }
   __syncthreads();
   auto pivot_recip = [&](df p, int j) {
     if (!(p.hi > 0.f) || !isfinite(p.hi)) {
@@ -311,48 +316,46 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
       atomicMin(&s.info[1], kt * TB + j);
       p = df_make(1.f, 0.f);
     }
-    const df r = df_recip(p);
+    const df r = dg_recip(p);
     rpa[j] = make_float2(r.hi, r.lo);
   };
+  // owned elements: position p = tid + DG_THREADS q lies in column c = 63 - w, w the largest
+  // integer with w (w + 1) / 2 <= p, at row c + p - w (w + 1) / 2
+  df av[NQ];
+  int pq[NQ], rof[NQ], cof[NQ], col[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int p = tid + DG_THREADS * q;
+    pq[q] = p < NTRI ? p : NTRI;           // NTRI: never in a step's prefix
+    int w = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    if (w > TB - 1) w = TB - 1;
+    if (w < 0) w = 0;
+    if ((w + 1) * (w + 2) / 2 <= p && w < TB - 1) ++w;
+    if (w * (w + 1) / 2 > p && w > 0) --w;
+    const int c = TB - 1 - w, i = min(c + p - w * (w + 1) / 2, TB - 1);
+    rof[q] = i * DG_LD;
+    cof[q] = c * DG_LD;
+    col[q] = c;
+    av[q] = p < NTRI ? dg_ld(t, i, c) : df_make(0.f, 0.f);
+  }
   if (tid == 0) pivot_recip(dg_ld(t, 0, 0), 0);
   __syncthreads();
   // ---- factor: 63 elimination steps, one barrier each ----
   for (int j = 0; j < TB - 1; ++j) {
-    const df r = df_make(rpa[j].x, rpa[j].y);
-    const int w = TB - 1 - j;              // columns j+1 .. 63: w of them
-    const int cnt = w * (w + 1) / 2;
-    const int pidx = cnt - w;              // position of (j+1, j+1): first of column j+1
-    if (tid == 0) {
-      const df aij = dg_ld(t, j + 1, j);
-      const df v = df_add_fast(dg_ld(t, j + 1, j + 1), df_neg(df_mul(df_mul(aij, r), aij)));
-      dg_st(t, j + 1, j + 1, v);
-      pivot_recip(v, j + 1);
-    } else {
-      // elements (tid - 1) + NW q of the step's list without its pivot, all loaded first
-      constexpr int EPT = (NTRI - TB + NW - 1) / NW;
-      const int nq = (cnt - 1 + NW - 1) / NW;  // block-uniform
-      df a[EPT], u[EPT], b[EPT];
-      int pos[EPT];
+    const int w = TB - 1 - j;                // columns j+1 .. 63: w of them
+    const int cnt = w * (w + 1) / 2;         // the step's prefix of the list
+    const int nxt = cnt - w;                 // column j+1 starts here, with its pivot
+    if (tid < cnt) {
+      const df r = df_make(rpa[j].x, rpa[j].y);
 #pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        pos[q] = -1;
-        if (q < nq) {
-          int e = tid - 1 + NW * q;
-          e += e >= pidx;
-          if (e < cnt) {
-            const int ic = tab[e], i = ic >> 8, c = ic & 255;
-            pos[q] = i * DG_LD + c;
-            a[q] = dg_ld(t, i, c);
-            u[q] = dg_ld(t, i, j);
-            b[q] = dg_ld(t, c, j);
+      for (int q = 0; q < NQ; ++q)
+        if (pq[q] < cnt) {
+          const df u = dg_ld(t, 0, rof[q] + j), b = dg_ld(t, 0, cof[q] + j);
+          av[q] = df_add_fast(av[q], df_neg(df_mul(df_mul(u, r), b)));
+          if (pq[q] >= nxt) {                // column j+1: final now
+            dg_st(t, 0, rof[q] + col[q], av[q]);
+            if (pq[q] == nxt) pivot_recip(av[q], j + 1);
           }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (q < nq && pos[q] >= 0) {
-          const df v = df_add_fast(a[q], df_neg(df_mul(df_mul(u[q], r), b[q])));
-          t[pos[q]] = make_float2(v.hi, v.lo);
         }
     }
     __syncthreads();
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
   if (tid < TB) {
     df p = dg_ld(t, tid, tid);
     if (!(p.hi > 0.f) || !isfinite(p.hi)) p = df_make(1.f, 0.f);
-    const df d = df_sqrt(p), rd = df_recip(d);
+    const df d = df_sqrt(p), rd = dg_recip(d);
     dsq[tid] = make_float2(d.hi, d.lo);
     rdq[tid] = make_float2(rd.hi, rd.lo);
   }
@@ -380,7 +383,10 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     base[(size_t)i * M.ld + c] = make_float2(v.hi, v.lo);
   }
   // ---- Y = L1^-1 in place, level by level (unit diagonal implicit); level s has 64 / (2 s)
-  // blocks of s x s outputs, 32 s in all, OPT = 1024 / DG_THREADS of them per thread at most ----
+  // blocks of s x s outputs, 32 s in all, OPT = 1024 / DG_THREADS of them per thread at most.
+  // In T the sum's length depends on the column, in Y21 on the row: the index that sets it is
+  // the slow one (one value per warp at s = 32), so a warp's lanes run equal loops; each sum
+  // runs in two interleaved accumulators ----
   constexpr int OPT = (32 * 32 + DG_THREADS - 1) / DG_THREADS;
   for (int sz = 1; sz < TB; sz <<= 1) {
     const int lg = __ffs(sz) - 1;          // sz = 2^lg
@@ -391,11 +397,16 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     for (int q = 0; q < OPT; ++q) {
       const int e = tid + DG_THREADS * q;
       if (e < nel) {
-        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem & (sz - 1), c = rem >> lg;
         const int p = blk * 2 * sz, row = p + sz + r;
-        df acc = dg_ld(t, row, p + c);
-        for (int k = c + 1; k < sz; ++k) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
-        tv[q] = acc;
+        df acc = dg_ld(t, row, p + c), acc2 = df_make(0.f, 0.f);
+        int k = c + 1;
+        for (; k + 1 < sz; k += 2) {
+          acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
+          acc2 = df_add_fast(acc2, df_mul(dg_ld(t, row, p + k + 1), dg_ld(t, p + k + 1, p + c)));
+        }
+        if (k < sz) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + k), dg_ld(t, p + k, p + c)));
+        tv[q] = df_add_fast(acc, acc2);
       }
     }
     __syncthreads();
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     for (int q = 0; q < OPT; ++q) {
       const int e = tid + DG_THREADS * q;
       if (e < nel) {
-        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
+        const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem & (sz - 1), c = rem >> lg;
         const int p = blk * 2 * sz;
         dg_st(t, p + sz + r, p + c, tv[q]);
       }
@@ -416,9 +427,14 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
       if (e < nel) {
         const int blk = e >> (2 * lg), rem = e & (sz * sz - 1), r = rem >> lg, c = rem & (sz - 1);
         const int p = blk * 2 * sz, row = p + sz + r;
-        df acc = dg_ld(t, row, p + c);
-        for (int k = 0; k < r; ++k) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
-        tv[q] = df_neg(acc);
+        df acc = dg_ld(t, row, p + c), acc2 = df_make(0.f, 0.f);
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+          acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
+          acc2 = df_add_fast(acc2, df_mul(dg_ld(t, row, p + sz + k + 1), dg_ld(t, p + sz + k + 1, p + c)));
+        }
+        if (k < r) acc = df_add_fast(acc, df_mul(dg_ld(t, row, p + sz + k), dg_ld(t, p + sz + k, p + c)));
+        tv[q] = df_neg(df_add_fast(acc, acc2));
       }
     }
     __syncthreads();
