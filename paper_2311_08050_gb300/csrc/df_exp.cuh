@@ -5,6 +5,10 @@
 // double-float so that r is accurate; then exp(r) = (exp(r / 4))^4, the inner factor by its
 // Taylor series to degree 10 (|r / 4| <= 0.0867: the first dropped term is below 2^-64), two
 // squarings (each doubles the relative error, so few of them), and the exact scaling by 2^k.
+// The series' terms of degree 6 and up sum to less than 6e-10, so they are evaluated in FP32
+// (error below 2^-52 of the result); the degrees 5 .. 0 run in double-float by Horner's rule,
+// each step adding a coefficient to a product at most 0.1 of it, so the leading words add by
+// the fast two-sum.
 #pragma once
 #include "df64.cuh"
 
@@ -22,11 +26,20 @@ static __device__ __forceinline__ df df_exp_neg(df x) {
   // Taylor coefficients 1/n!, n = 0..10, as double-float
   constexpr double c[11] = {1.0,           1.0,            0.5,             1.0 / 6.0,        1.0 / 24.0,        1.0 / 120.0,
                             1.0 / 720.0,   1.0 / 5040.0,   1.0 / 40320.0,   1.0 / 362880.0,   1.0 / 3628800.0};
-  df p = df_make((float)c[10], (float)(c[10] - (double)(float)c[10]));
+  float tail = (float)c[10];
 #pragma unroll
-  for (int n = 9; n >= 0; --n) {
+  for (int n = 9; n >= 6; --n) tail = __fmaf_rn(tail, u.hi, (float)c[n]);
+  df p = df_mul(df_make(tail, 0.f), u);
+#pragma unroll
+  for (int n = 5; n >= 0; --n) {
     const df cn = df_make((float)c[n], (float)(c[n] - (double)(float)c[n]));
-    p = df_add(df_mul(p, u), cn);
+    if (n < 5) p = df_mul(p, u);
+    // cn + p with |p| < |cn|: the leading words by the fast two-sum, then the low words
+    float sh, se;
+    fast_two_sum(cn.hi, p.hi, sh, se);
+    se = __fadd_rn(se, __fadd_rn(cn.lo, p.lo));
+    fast_two_sum(sh, se, sh, se);
+    p = df{sh, se};
   }
   p = df_mul(p, p);
   p = df_mul(p, p);

@@ -143,12 +143,11 @@ static int mixed_panel(Batch& B, const MRef& M, int c0, int c1) {
     Side side(B);
     OzOperand pa = operand(B.PA, B.EA, R > 0 ? R : 1, IB);
     if (R > 0) oz_slice_df(M.base, M.stride, M.ld, c0 + IB, c0, R, IB, false, pa, S, B.n, side.fork());
-    launch_potrf_diag_df(B.d_slots, B.n, M.sel, c0 / IB, B.st);
+    // the tile kernel also slices its inverse tile: the B operand of the panel product
+    OzOperand pb = operand(B.PB, B.EB, IB, IB);
+    launch_potrf_diag_df(B.d_slots, B.n, M.sel, c0 / IB, R > 0 ? &pb : nullptr, S, B.st);
     if (R <= 0) return INLA_OK;
     float2* panel = M.base + (int64_t)(c0 + IB) * M.ld + c0;
-    OzOperand pb = operand(B.PB, B.EB, IB, IB);
-    oz_slice_df(reinterpret_cast<float2*>(M.linv) + (int64_t)(c0 / IB) * IB * IB, M.linv_stride, IB, 0, 0, IB, IB,
-                false, pb, S, B.n, B.st);
     side.join();
     OzArgs a = gemm_args(B, panel, M.stride, M.ld, R, IB, IB, 0.f, 1.f);
     return oz_gemm(pa, pb, a, B.n, B.st);

@@ -7,6 +7,7 @@
 #include "device_util.cuh"
 #include "kernels.h"
 #include "mixed.h"
+#include "oz_slice.cuh"
 
 namespace inla {
 
@@ -274,7 +275,10 @@ __global__ void k_s_pad_identity(Slot* slots) {
 // written out and L1 is inverted in place by levels (s = 1, 2, .., 32: two inverted diagonal
 // blocks of size s and the block below them give the inverse of the 2s block, -Y22 L21 Y11), so
 // L^-1 = D^-1/2 Y.  Stores the factor tile (double-float, upper part zeroed) and the inverse tile
-// (double-float, in the FP64-sized cells of the inverse-tile array).
+// (double-float, in the FP64-sized cells of the inverse-tile array).  With `pb.planes` set it also
+// slices the inverse tile as the 64-row, K = 64 operand pb (one exponent per row, 8 values per
+// lane), exactly as the row slicer would from the stored tile; a slot that is inactive or has no
+// tile kt gets zero slices, so the product adds nothing to it.
 constexpr int DG_LD = TB + 1;
 constexpr int DG_THREADS = 1024;
 // 1 / a for the tile's pivot chain: the PTX approximate reciprocal (within 1 ulp over the whole
@@ -291,11 +295,28 @@ __device__ __forceinline__ df dg_recip(df a) {
 __device__ __forceinline__ df dg_ld(const float2* t, int i, int c) { return df_make(t[i * DG_LD + c].x, t[i * DG_LD + c].y); }
 __device__ __forceinline__ void dg_st(float2* t, int i, int c, df v) { t[i * DG_LD + c] = make_float2(v.hi, v.lo); }
 
-__global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int sel, int kt) {
+__device__ __forceinline__ void dg_zero_slices(const OzOperand& pb, int S) {
+  if (!pb.planes) return;
+  const int slot = blockIdx.x;
+  uint16_t* planes = pb.planes + (int64_t)slot * S * pb.plane_stride;
+  for (int e = threadIdx.x; e < S * TB * (TB / 8); e += blockDim.x) {
+    const int sl = e / (TB * (TB / 8)), rem = e % (TB * (TB / 8)), i = rem >> 3, g = rem & 7;
+    *reinterpret_cast<uint4*>(planes + sl * pb.plane_stride + (int64_t)i * pb.ld_k + 8 * g) = make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x < TB) pb.exps[slot * pb.exp_slot_stride + threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int sel, int kt, OzOperand pb, int S) {
   const Slot& s = slots[blockIdx.x];
-  if (!s.active) return;
+  if (!s.active) {
+    dg_zero_slices(pb, S);
+    return;
+  }
   DfRef M = df_ref(s, sel);
-  if (kt * TB >= M.n) return;
+  if (kt * TB >= M.n) {
+    dg_zero_slices(pb, S);
+    return;
+  }
   constexpr int NTRI = TB * (TB + 1) / 2;  // 2080 lower-triangle elements (diagonal included)
   constexpr int NQ = (NTRI + DG_THREADS - 1) / DG_THREADS;  // positions per thread
   __shared__ float2 t[TB * DG_LD];
@@ -449,14 +470,37 @@ __global__ void __launch_bounds__(DG_THREADS) k_potrf_diag_df(Slot* slots, int s
     }
     __syncthreads();
   }
-  // ---- L^-1 = D^-1/2 Y ----
+  // ---- L^-1 = D^-1/2 Y: lane (row i, group g) holds columns 8g .. 8g + 7 of row i ----
   float2* linv = reinterpret_cast<float2*>(M.Linv) + (size_t)kt * TB * TB;
-  for (int e = tid; e < TB * TB; e += DG_THREADS) {
-    const int i = e >> 6, c = e & 63;
-    df v = df_make(0.f, 0.f);
-    if (c < i) v = df_mul(dg_ld(t, i, c), df_make(rdq[i].x, rdq[i].y));
-    else if (c == i) v = df_make(rdq[i].x, rdq[i].y);
-    linv[i * TB + c] = make_float2(v.hi, v.lo);
+  static_assert(DG_THREADS >= TB * (TB / 8), "one lane per 8 values of the tile");
+  if (tid < TB * (TB / 8)) {
+    const int i = tid >> 3, g = tid & 7;
+    const df ri = df_make(rdq[i].x, rdq[i].y);
+    df x[8];
+    float mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = 8 * g + k;
+      df v = df_make(0.f, 0.f);
+      if (c < i) v = df_mul(dg_ld(t, i, c), ri);
+      else if (c == i) v = ri;
+      x[k] = v;
+      mx = fmaxf(mx, fabsf(v.hi));
+    }
+    float4* dst = reinterpret_cast<float4*>(linv + i * TB + 8 * g);  // 64-byte aligned
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) dst[k / 2] = make_float4(x[k].hi, x[k].lo, x[k + 1].hi, x[k + 1].lo);
+    if (pb.planes) {
+      // the row's exponent over its 8 lanes (aligned groups of 8 within the warp)
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // |x| <= |hi| (1 + 2^-24): round the bound up so that |x| 2^-e <= 1 holds
+      const int e = chunk_exponent(mx * (1.0f + 1.2e-7f));
+      const int slot = blockIdx.x;
+      if (g == 0) pb.exps[slot * pb.exp_slot_stride + i] = e;
+      slice_and_store(x, e, pb.planes + (int64_t)slot * S * pb.plane_stride, pb.plane_stride, S,
+                      (int64_t)i * pb.ld_k + 8 * g, true);
+    }
   }
 }
 
@@ -729,8 +773,10 @@ void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st) {
 void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st) {
   count_launch("k_s_pad_identity"), k_s_pad_identity<<<dim3(vgrid(max_k), nslots), 256, 0, st>>>(slots);
 }
-void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st) {
-  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, DG_THREADS, 0, st>>>(slots, sel, kt);
+void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, const OzOperand* slices, int S, cudaStream_t st) {
+  OzOperand pb{};
+  if (slices) pb = *slices;
+  count_launch("k_potrf_diag_df"), k_potrf_diag_df<<<nslots, DG_THREADS, 0, st>>>(slots, sel, kt, pb, S);
 }
 int launch_trsv_df(const TrsvArgs& a, cudaStream_t st) {
   // resident blocks per SM and SM count, per device (the cooperative grid must fit at once)

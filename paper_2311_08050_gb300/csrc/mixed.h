@@ -16,7 +16,9 @@ void launch_qp_gemv_df(Slot* slots, int nslots, int which, int max_n, cudaStream
 void launch_z_gemv_df(Slot* slots, int nslots, int max_n, cudaStream_t st);
 void launch_ct_fill_df(Slot* slots, int nslots, int max_k, cudaStream_t st);
 void launch_s_pad_identity(Slot* slots, int nslots, int max_k, cudaStream_t st);
-void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, cudaStream_t st);
+// factor diagonal tile kt of every slot; with `slices` non-null, also write the tile inverse's S
+// slices into that operand (64 rows, K = 64): the B operand of the panel product X = A L^-T
+void launch_potrf_diag_df(Slot* slots, int nslots, int sel, int kt, const OzOperand* slices, int S, cudaStream_t st);
 // triangular solve with a double-float factor (one cooperative launch; see k_df.cu)
 struct TrsvArgs {
   Slot* slots;
