@@ -227,11 +227,11 @@ const char *inla_status_string(int status);
  *  Every intermediate lives in one static device array of ~7.4 MB that each GPU loading the
  *  library holds until the process exits; the call allocates nothing (no cudaMalloc, no
  *  library allocator).  The first call on a device looks that array's address up
- *  (cudaGetSymbolAddress), so make it before any stream capture; host threads may make their
- *  first calls at the same time (the address is stored atomically).  All calls share the array
- *  and it keeps the last call's contents: calls that overlap on the GPU (other streams,
- *  other host threads) race.  The call synchronizes `stream` before returning;
- *  INLA_E_TIMEOUT if a bounded device-side wait gave up. */
+ *  (cudaGetSymbolAddress); host threads may make their first calls at the same time (the
+ *  address is stored atomically).  All calls share the array and it keeps the last call's
+ *  contents: calls that overlap on the GPU (other streams, other host threads) race.  The call
+ *  reads its error flag back to the host and synchronizes `stream` before returning, so it
+ *  cannot be captured into a CUDA graph; INLA_E_TIMEOUT if a bounded device-side wait gave up. */
 int inla_ozaki_gemm_noalloc(const double *A, const double *B, double *C, int32_t M, int32_t N, int32_t K,
                             int32_t slices, void *stream);
 
