@@ -204,7 +204,7 @@ static int mixed_potrf_launches(Batch& B, int sel, int nb) {
   return INLA_OK;
 }
 
-// The blocked Cholesky issues ~1500 launches at n = 16384 whose sequence depends only on the
+// The blocked Cholesky issues ~1300 launches at n = 16384 whose sequence depends only on the
 // batch layout (buffers, strides, slot count), the matrix selected and the slice count.  The
 // first call with a layout runs the launches; the second captures them into a CUDA graph
 // (stream capture, this thread only) and every later call replays it.  Off when the per-kernel
