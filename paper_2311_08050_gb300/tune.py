@@ -23,11 +23,24 @@ import numpy as np
 
 from . import inla
 
-# (prior_slices, gram_slices, slices, newton_slices, var_slices) from the cheapest up, by the GEMM
-# passes S (S + 1) / 2 weighted with each phase's share of the algorithmic flops of an FD batch:
-# the prior covariance's factorisation and inverse 2 n^3 / 3, the product W^T W n^3 / 3, the
-# factor at the mode n^3 / 3, its inverse n^3 / 3, the leading point's Newton factorisations
-# ~0.2 n^3 per point
+# (prior_slices, gram_slices, slices, newton_slices, var_slices) from the cheapest up by
+# candidate_cost: the GEMM passes S (S + 1) / 2 of each phase weighted with its work per point of
+# an FD batch -- the prior covariance's factorisation and inverse 2 n^3 / 3, the product W^T W
+# n^3 / 3, the factor at the mode n^3 / 3, its inverse n^3 / 3 -- and the leading point's Newton
+# factorisations at NEWTON_WEIGHT n^3 per point: four factorisations of one point in nine, whose
+# single-slot launches run at about half the batched rate per flop (at n = 16384 that phase takes
+# 148 ms per batch, as long as ~0.7 n^3 per point of batched work at 5 slices)
+NEWTON_WEIGHT = 0.7
+
+
+def candidate_cost(setting) -> float:
+    """Relative GEMM cost per point of an FD batch of a (prior, gram, final, Newton, variance)
+    slice setting, in units of n^3 BF16 passes."""
+    p, g, s, nw, v = setting
+    passes = lambda k: k * (k + 1) / 2
+    return (2 * passes(p) + passes(g) + passes(s) + passes(v)) / 3 + NEWTON_WEIGHT * passes(nw)
+
+
 CANDIDATES = [(4, 4, 4, 3, 3), (4, 4, 4, 3, 4), (4, 5, 4, 3, 4), (4, 4, 5, 3, 4), (4, 5, 5, 3, 3), (4, 4, 4, 4, 4),
               (4, 5, 5, 3, 4), (5, 5, 4, 3, 4), (5, 5, 5, 3, 3), (4, 5, 5, 4, 4), (5, 5, 5, 3, 4), (5, 5, 5, 3, 5),
               (5, 5, 5, 4, 4), (5, 5, 5, 4, 5), (6, 6, 5, 4, 5), (6, 6, 6, 4, 6)]
